@@ -1,0 +1,261 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check is a closed form, a
+library routine reached by a different route, a dense assembled solve, a value
+printed in the paper (Table 1, tests/golden/), a convergence order, or an
+invariant.  The last test plants plausible mistakes in oracle building blocks
+and checks that the pins catch each of them.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import (
+    apply_h,
+    apply_weak,
+    dense_solve,
+    diff_matrix,
+    fast_solve,
+    gll_nodes_weights,
+    l2_error_table1,
+    refined_solve,
+    sem_1d,
+)
+from oracle.sem import Sem1D, apply_mass
+from paper_2310_00226_gb300.inputs import random_rhs, sine_123, table1_dirichlet, table1_neumann
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- GLL rule
+
+def test_gll_small_closed_forms():
+    r, w = gll_nodes_weights(1)
+    np.testing.assert_allclose(r, [-1, 1], atol=0)
+    np.testing.assert_allclose(w, [1, 1], rtol=1e-15)
+    r, w = gll_nodes_weights(2)
+    np.testing.assert_allclose(r, [-1, 0, 1], atol=1e-15)
+    np.testing.assert_allclose(w, [1 / 3, 4 / 3, 1 / 3], rtol=1e-14)
+    # N = 3: interior nodes +-1/sqrt(5), weights 1/6, 5/6.
+    r, w = gll_nodes_weights(3)
+    np.testing.assert_allclose(r, [-1, -1 / math.sqrt(5), 1 / math.sqrt(5), 1], atol=1e-15)
+    np.testing.assert_allclose(w, [1 / 6, 5 / 6, 5 / 6, 1 / 6], rtol=1e-14)
+
+
+@pytest.mark.parametrize("N", list(range(1, 21)))
+def test_gll_exactness_degree_2N_minus_1(N):
+    r, w = gll_nodes_weights(N)
+    assert np.all(np.diff(r) > 0)
+    for p in range(0, 2 * N):
+        exact = 0.0 if p % 2 else 2.0 / (p + 1)
+        assert abs(np.dot(w, r**p) - exact) < 1e-13 * max(1, N), (N, p)
+    # Degree 2N: the Lobatto error term (Abramowitz & Stegun 25.4.32) with
+    # f^(2N) = (2N)! gives the quadrature error of x^(2N) in closed form.
+    err = np.dot(w, r ** (2 * N)) - 2.0 / (2 * N + 1)
+    closed = ((N + 1) * N**3 * 2.0 ** (2 * N + 1) * math.factorial(N - 1) ** 4
+              / ((2 * N + 1) * math.factorial(2 * N) ** 2))
+    assert abs(err - closed) < 1e-13 + 1e-10 * closed, (N, err, closed)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 8, 13, 20])
+def test_gll_nodes_are_roots_of_legendre_derivative(N):
+    # Independent route: numpy's Legendre class, roots of P_N'.
+    r, _ = gll_nodes_weights(N)
+    roots = np.sort(np.polynomial.legendre.Legendre.basis(N).deriv().roots().real)
+    np.testing.assert_allclose(r[1:-1], roots, atol=1e-13)
+
+
+# ---------------------------------------------------------------- D matrix
+
+@pytest.mark.parametrize("N", [1, 2, 4, 6, 10, 16])
+def test_diff_matrix_exact_on_polynomials(N):
+    r, _ = gll_nodes_weights(N)
+    D = diff_matrix(r)
+    for m in range(0, N + 1):
+        du = D @ r**m
+        exact = m * r ** (m - 1) if m > 0 else np.zeros_like(r)
+        assert np.max(np.abs(du - exact)) < 1e-12 * max(1, m) * N**2, (N, m)
+
+
+# ---------------------------------------------------------------- 1D matrices
+
+@pytest.mark.parametrize("k,Ne", [(1, 5), (2, 4), (4, 3), (6, 2)])
+def test_neumann_matrices_properties(k, Ne):
+    s = sem_1d(k, Ne, 0.0, 1.0, bc="neumann")
+    assert s.n == Ne * k + 1
+    np.testing.assert_allclose(s.S, s.S.T, atol=1e-12)
+    np.testing.assert_allclose(s.S.sum(axis=1), 0.0, atol=1e-10 * np.abs(s.S).max())
+    assert np.all(s.M > 0)
+    assert abs(s.M.sum() - 1.0) < 1e-14
+    # u^T S u = int_0^1 (u')^2 exactly for a global polynomial of degree <= k.
+    if k >= 2:
+        u = s.x**2
+        assert abs(u @ s.S @ u - 4.0 / 3.0) < 1e-12
+    # Lumped mass integrates degree 2k-1 exactly: sum M x^(2k-1) = 1/(2k).
+    assert abs(np.dot(s.M, s.x ** (2 * k - 1)) - 1.0 / (2 * k)) < 1e-13
+
+
+def test_dirichlet_dof_counts_match_table1():
+    # Table 1 lists 9^3 (Q5, 2^3 mesh) ... 191^3 (Q6, 32^3 mesh): n = Ne*k - 1.
+    for k, Ne, n in [(5, 2, 9), (5, 32, 159), (6, 2, 11), (6, 32, 191)]:
+        assert sem_1d(k, Ne, -1.0, 1.0).n == n
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 31, 100])
+def test_k1_closed_form_eigenpairs(n):
+    # Q^1 with Dirichlet data on [0,1], Ne = n + 1: S = tridiag(-1,2,-1)/h,
+    # M = h I, so lambda_j = (2 - 2 cos(j pi h)) / h^2 and the eigenvectors are
+    # the DST-I columns sin(i j pi h).
+    s = sem_1d(1, n + 1, 0.0, 1.0)
+    h = 1.0 / (n + 1)
+    j = np.arange(1, n + 1)
+    lam = (2 - 2 * np.cos(j * np.pi * h)) / h**2
+    np.testing.assert_allclose(s.lam, lam, rtol=2e-13, atol=1e-9)
+    i = np.arange(1, n + 1)
+    V = np.sin(np.outer(i, j) * np.pi * h)
+    V /= np.linalg.norm(V, axis=0)
+    # Same columns up to sign (all eigenvalues are simple).
+    d = np.abs(np.sum(V * s.Q, axis=0))
+    np.testing.assert_allclose(d, 1.0, atol=1e-11)
+
+
+@pytest.mark.parametrize("k,Ne", [(2, 16), (4, 10), (6, 5), (20, 4)])
+def test_eigendecomposition_identities(k, Ne):
+    s = sem_1d(k, Ne, 0.0, 1.0)
+    n = s.n
+    scale = s.lam.max()
+    # S T = M T Lambda (Eq. 6 of Section 2.2) and T T^{-1} = I (Section 2.3).
+    res = s.S @ s.T - s.M[:, None] * s.T * s.lam[None, :]
+    assert np.abs(res).max() / (scale * np.abs(s.M[:, None] * s.T).max()) < 1e-13 * n
+    np.testing.assert_allclose(s.T @ s.Tinv, np.eye(n), atol=1e-12 * n)
+    np.testing.assert_allclose(s.Q.T @ s.Q, np.eye(n), atol=1e-13 * n)
+    assert np.all(np.diff(s.lam) > 0)
+    # Smallest eigenvalue approximates the continuous one, pi^2 on [0,1];
+    # Q^20 robustness (Section 3.4).
+    assert abs(s.lam[0] - np.pi**2) < 1e-3
+
+
+def test_smallest_eigenvalue_headline_grid():
+    s = sem_1d(4, 250, 0.0, 1.0)
+    assert s.n == 999
+    assert abs(s.lam[0] - np.pi**2) < 1e-9
+    # The largest mode grows like h^-2: kappa of the 1D operator ~ 1e6.
+    assert 1e6 < s.lam[-1] / s.lam[0] < 2e6
+
+
+# ---------------------------------------------------------------- 3D solve
+
+def _boxes():
+    return [
+        # (kx,Nex,Lx), (ky,Ney,Ly), (kz,Nez,Lz), c, bc
+        ((2, 3, 1.0), (3, 2, 0.7), (1, 6, 1.3), 0.0, "dirichlet"),
+        ((4, 2, 2.0), (2, 4, 1.0), (3, 3, 0.5), 2.5, "dirichlet"),
+        ((5, 2, 1.0), (5, 2, 1.0), (5, 2, 1.0), 1.0, "dirichlet"),
+        ((2, 3, 1.0), (3, 2, 0.7), (1, 5, 1.3), 1.0, "neumann"),
+    ]
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_fast_solve_matches_dense_lu(case):
+    (bx, by, bz, c, bc) = _boxes()[case]
+    sx = sem_1d(bx[0], bx[1], 0.0, bx[2], bc)
+    sy = sem_1d(by[0], by[1], 0.0, by[2], bc)
+    sz = sem_1d(bz[0], bz[1], 0.0, bz[2], bc)
+    F = random_rhs(sx.n, sy.n, sz.n, seed=case)
+    u_ref = dense_solve(F, sx, sy, sz, c)
+    for u in (fast_solve(F, sx, sy, sz, c), refined_solve(F, sx, sy, sz, c, 1)):
+        assert np.abs(u - u_ref).max() / np.abs(u_ref).max() < 1e-11
+
+
+def test_operators_match_kronecker_assembly():
+    sx, sy, sz = sem_1d(2, 3, 0.0, 1.0), sem_1d(3, 2, 0.0, 0.8), sem_1d(4, 2, 0.0, 1.2)
+    c = 0.75
+    U = random_rhs(sx.n, sy.n, sz.n, seed=7)
+    Ix, Iy, Iz = (np.eye(s.n) for s in (sx, sy, sz))
+    Hk = (c * np.eye(U.size) + np.kron(Iz, np.kron(Iy, sx.H)) + np.kron(Iz, np.kron(sy.H, Ix))
+          + np.kron(sz.H, np.kron(Iy, Ix)))
+    np.testing.assert_allclose(apply_h(U, sx, sy, sz, c).ravel(), Hk @ U.ravel(), rtol=1e-12, atol=1e-10)
+    Mx, My, Mz = (np.diag(s.M) for s in (sx, sy, sz))
+    Ak = (c * np.kron(Mz, np.kron(My, Mx)) + np.kron(Mz, np.kron(My, sx.S))
+          + np.kron(Mz, np.kron(sy.S, Mx)) + np.kron(sz.S, np.kron(My, Mx)))
+    np.testing.assert_allclose(apply_weak(U, sx, sy, sz, c).ravel(), Ak @ U.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def _table1_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_l2_errors.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, Ne, bc, n, err = line.split()
+                rows.append((int(k), int(Ne), bc, int(n), float(err)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _table1_rows(), ids=lambda r: f"Q{r[0]}-Ne{r[1]}-{r[2]}")
+def test_table1_l2_errors(row):
+    k, Ne, bc, n, err_paper = row
+    s = sem_1d(k, Ne, -1.0, 1.0, bc)
+    assert s.n == n
+    gen = table1_dirichlet if bc == "dirichlet" else table1_neumann
+    u, f = gen(s.x, s.x, s.x, 1.0)
+    uh = refined_solve(f, s, s, s, 1.0, sweeps=1)
+    err = l2_error_table1(uh - u, Ne)
+    # Three printed digits: rounding is <= 0.5% of the value.  The two finest
+    # Q^6 rows sit at the rounding floor of an FP64 solve (~5e-11), where the
+    # paper's unrefined solve and ours differ in the last digit: 1%.
+    tol = 0.01 if err_paper < 1e-10 else 0.006
+    assert abs(err - err_paper) <= tol * err_paper, (err, err_paper)
+
+
+def test_convergence_order_k_plus_2():
+    # Section 3.1: Q^k SEM (k >= 2) is (k+2)-th order in the nodal l2 error.
+    for k, nes in [(2, (8, 16)), (3, (4, 8))]:
+        errs = []
+        for Ne in nes:
+            s = sem_1d(k, Ne, 0.0, 1.0)
+            u, f = sine_123(s.x, s.x, s.x)
+            uh = fast_solve(f, s, s, s, 0.0)
+            errs.append(np.sqrt(np.mean((uh - u) ** 2)))
+        order = math.log2(errs[0] / errs[1])
+        assert abs(order - (k + 2)) < 0.35, (k, order)
+
+
+def test_residual_invariant_after_refinement():
+    s = sem_1d(2, 32, 0.0, 1.0)
+    u_ex, f = sine_123(s.x, s.x, s.x)
+    u = refined_solve(f, s, s, s, 0.0, sweeps=1)
+    Mf = apply_mass(f, s, s, s)
+    rel = np.abs(apply_weak(u, s, s, s, 0.0) - Mf).max() / np.abs(Mf).max()
+    assert rel < 50 * np.finfo(float).eps * s.n
+    # The discrete solution approximates u to the Q^2 accuracy at h = 1/64.
+    assert np.abs(u - u_ex).max() < 2e-5
+
+
+# ---------------------------------------------------------------- teeth
+
+def _planted(s: Sem1D, what: str) -> Sem1D:
+    import dataclasses
+    if what == "transposed_Tinv":
+        return dataclasses.replace(s, Tinv=s.T.T.copy())
+    if what == "no_mass_scaling":
+        return dataclasses.replace(s, T=s.Q.copy(), Tinv=s.Q.T.copy())
+    if what == "reversed_lambda":
+        return dataclasses.replace(s, lam=s.lam[::-1].copy())
+    if what == "unsorted_T":
+        return dataclasses.replace(s, T=s.T[:, ::-1].copy())
+    raise ValueError(what)
+
+
+@pytest.mark.parametrize("what", ["transposed_Tinv", "no_mass_scaling", "reversed_lambda", "unsorted_T"])
+def test_pins_catch_planted_mistakes(what):
+    sx, sy, sz = sem_1d(2, 3, 0.0, 1.0), sem_1d(3, 2, 0.0, 0.7), sem_1d(4, 2, 0.0, 1.2)
+    F = random_rhs(sx.n, sy.n, sz.n, seed=3)
+    u_ref = dense_solve(F, sx, sy, sz, 0.5)
+    bad = fast_solve(F, _planted(sx, what), sy, sz, 0.5)
+    assert np.abs(bad - u_ref).max() / np.abs(u_ref).max() > 1e-3
+    # and a dropped shift term
+    bad_c = fast_solve(F, sx, sy, sz, 0.0)
+    assert np.abs(bad_c - u_ref).max() / np.abs(u_ref).max() > 1e-3
