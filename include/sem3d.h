@@ -1,0 +1,146 @@
+/*
+ * libsem3d -- fast-diagonalisation direct solver for Q^k spectral-element
+ * discretisations of (-Lap + c) u = f on a box, homogeneous Dirichlet data.
+ *
+ * Method: Liu, Shen, Zhang, "A simple GPU implementation of spectral-element
+ * methods for solving 3D Poisson type equations on rectangular domains and its
+ * applications", arXiv 2310.00226.
+ *   - Section 2.1, Eq. (2)-(4): Q^k SEM = continuous Q^k FEM with (k+1)-point
+ *     Gauss-Lobatto quadrature; the 1D mass matrix M is diagonal.
+ *   - Section 2.2, Eq. (6)-(9): H = M^{-1} S = T Lambda T^{-1} from the
+ *     generalised eigenproblem S v = lambda M v.
+ *   - Section 2.3: robust form S1 = M^{-1/2} S M^{-1/2} = Q Lambda Q^T,
+ *     T = M^{-1/2} Q, T^{-1} = Q^T M^{1/2}.
+ *   - Section 2.4, Eq. (12)-(13): (c + H_x (+) H_y (+) H_z) u = f is solved by
+ *     three mode products with T^{-1}, an entrywise division by
+ *     lambda_x,i + lambda_y,j + lambda_z,l + c, and three mode products with T.
+ *
+ * Conventions shared by every call:
+ *   - Grid functions are dense FP64 arrays of the interior nodes, x fastest:
+ *     u[i + nx*(j + ny*l)], 0 <= i < nx, ... (the paper's vec(U), Section 2.4).
+ *     Boundary values are zero and not stored.  n_axis = Ne_axis * k - 1.
+ *   - Device pointers are CUDA global-memory pointers of the current device;
+ *     the caller owns them.  Host pointers are ordinary CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *     Work is enqueued on it; calls return without synchronising the host
+ *     unless stated otherwise.
+ *   - Every call returns a sem3d_status; on failure sem3d_last_error() gives a
+ *     message (thread-local).  Asynchronous CUDA faults surface as
+ *     SEM3D_ERR_CUDA on a later call.  No C++ exception crosses this boundary.
+ *   - A handle is not thread-safe; calls on one handle must be serialised by
+ *     the caller (they may target different streams one after another).
+ */
+#ifndef SEM3D_H
+#define SEM3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sem3d_plan* sem3d_handle;
+
+typedef enum {
+  SEM3D_OK = 0,
+  SEM3D_ERR_INVALID_ARG = 1,   /* bad size, pointer, axis, shift or mode     */
+  SEM3D_ERR_CUDA = 2,          /* a CUDA runtime/driver call failed          */
+  SEM3D_ERR_OOM = 3,           /* device or host allocation failed           */
+  SEM3D_ERR_NOT_CONVERGED = 4, /* refinement residual grew or became NaN/Inf */
+  SEM3D_ERR_TIMEOUT = 5,       /* a kernel's bounded wait expired            */
+  SEM3D_ERR_UNSUPPORTED = 6    /* mode not available for this size / device  */
+} sem3d_status;
+
+/* Arithmetic of the six mode products of one solve (Section 2.4, Eq. 13).
+ *   SEM3D_FP64   : FP64 operands and accumulation (mma.sync DMMA).
+ *   SEM3D_BF16X3 : operands split x = hi + lo into two bfloat16 numbers;
+ *                  hi*hi + hi*lo + lo*hi accumulated in FP32 on tcgen05
+ *                  tensor cores (about 16 significant bits per pass).
+ * FP64 accuracy is recovered by iterative refinement (sem3d_set_precision). */
+typedef enum {
+  SEM3D_FP64 = 0,
+  SEM3D_BF16X3 = 5
+} sem3d_precision;
+
+/* Build a plan: 1D GLL nodes, stiffness S, lumped mass M and the robust
+ * eigenbasis T, T^{-1}, lambda of each axis in FP64 on the host (Section 2.3,
+ * Appendix), then upload them to the current device.
+ *   nx, ny, nz : interior nodes per axis; each must satisfy (n+1) % k == 0,
+ *                n >= 1, and nx*ny*nz < 2^40.
+ *   k          : polynomial degree, 1 <= k <= 24.
+ *   Lx, Ly, Lz : box [0,Lx] x [0,Ly] x [0,Lz], each > 0.
+ *   c          : shift of -Lap + c; requires c > -(lambda_x,1 + lambda_y,1 +
+ *                lambda_z,1) so that the operator is positive definite.
+ *   out        : receives the handle (owned by the caller, freed by
+ *                sem3d_destroy).
+ * Synchronous with respect to the host.  Default mode: SEM3D_FP64, 1 sweep. */
+sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, double Lz, double c,
+                         sem3d_handle* out);
+
+/* Select the arithmetic of the mode products and the number of FP64
+ * iterative-refinement sweeps (each sweep: FP64 residual r = f - (c + H_x (+)
+ * H_y (+) H_z) u with the banded operator of Eq. 12, a solve of the correction
+ * in the selected arithmetic, u += correction).  sweeps in [0, 16].
+ * With a fixed sweep count the solve performs no host synchronisation. */
+sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
+
+/* Bytes of device workspace that sem3d_solve needs in the current mode. */
+sem3d_status sem3d_workspace_size(sem3d_handle h, size_t* bytes);
+
+/* Hand the plan a caller-owned device workspace of at least
+ * sem3d_workspace_size bytes (256-byte aligned); it stays owned by the caller
+ * and must outlive every solve that uses it.  Without this call the plan
+ * allocates its own workspace on the first solve (cudaMalloc). */
+sem3d_status sem3d_set_workspace(sem3d_handle h, void* dptr, size_t bytes);
+
+/* Solve (c + H_x (+) H_y (+) H_z) u = f, equivalently the weak form
+ * A u = (M (x) M (x) M) f of Eq. 12 with the alpha term c M (x) M (x) M.
+ *   f, u : device FP64 arrays of nx*ny*nz values (layout above); f and u must
+ *          not overlap.  u is fully overwritten.
+ * Enqueued on `stream`; no host synchronisation. */
+sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* stream);
+
+/* Apply the discrete operator in H form: Au = c u + (H_x (+) H_y (+) H_z) u
+ * (Eq. 12 with H = M^{-1} S, banded, at most 2k+1 entries per row and axis),
+ * in FP64.  u, Au: device FP64 arrays, must not overlap. */
+sem3d_status sem3d_apply(sem3d_handle h, const double* u, double* Au, void* stream);
+
+/* Axis data (axis 0 = x, 1 = y, 2 = z), copied to host memory; synchronous.
+ *   x_host      : n_axis node coordinates of the interior nodes.
+ *   lambda_host : n_axis eigenvalues of H, ascending (may be NULL).
+ *   T_host      : n_axis*n_axis FP64, column-major, column j = eigenvector of
+ *                 lambda_j (T of Section 2.3); may be NULL. */
+sem3d_status sem3d_get_nodes(sem3d_handle h, int axis, double* x_host);
+sem3d_status sem3d_get_eigs(sem3d_handle h, int axis, double* lambda_host, double* T_host);
+
+/* Host only (no device needed): the 1D data of one axis exactly as
+ * sem3d_setup builds it for n interior nodes of degree k on [0, L] (GLL
+ * nodes by Newton's method, closed-form GLL differentiation matrix, assembled
+ * S and lumped M, Householder + implicit-QR eigen-decomposition of
+ * S1 = M^{-1/2} S M^{-1/2}; Section 2.3 and the Appendix of the paper).
+ * Output arrays (host, caller-allocated, any may be NULL):
+ *   x[n] nodes, M[n] mass diagonal, lambda[n] ascending eigenvalues,
+ *   T[n*n] column-major eigenvectors (column j <-> lambda_j, T = M^{-1/2} Q,
+ *   sign fixed so that the largest |entry| of each column is positive). */
+sem3d_status sem3d_axis_info(int n, int k, double L, double* x, double* M, double* lambda, double* T);
+
+/* Wait for the work enqueued on `stream` and report errors that kernels of
+ * this plan recorded on the device: SEM3D_ERR_TIMEOUT if a bounded wait inside
+ * a tensor-core kernel expired (the kernel then stopped early and its output
+ * is invalid), SEM3D_ERR_CUDA for an asynchronous CUDA error.  Clears the
+ * recorded flags.  Synchronous with respect to the host. */
+sem3d_status sem3d_sync_check(sem3d_handle h, void* stream);
+
+/* Release the plan and every device buffer it allocated (not caller-owned
+ * workspace).  Synchronises the device first.  NULL is accepted. */
+sem3d_status sem3d_destroy(sem3d_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sem3d_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM3D_H */

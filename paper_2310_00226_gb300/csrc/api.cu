@@ -1,0 +1,359 @@
+// C ABI of libsem3d: plan construction, workspace, and the orchestration of
+// one solve (Section 2.4, Eq. 13) plus FP64 iterative refinement.
+#include "sem3d_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+
+using namespace sem3d;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sem3d_status fail(sem3d_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+sem3d_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? SEM3D_ERR_OOM : SEM3D_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                                 \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr); \
+  } while (0)
+
+// Host-side cache of 1D axis data: identical (n, k, L) axes share one eigen-
+// decomposition within a process.
+std::mutex g_axis_mu;
+std::map<std::tuple<int, int, double>, std::shared_ptr<const Axis1D>> g_axis_cache;
+
+std::shared_ptr<const Axis1D> get_axis(int n, int k, double L) {
+  const auto key = std::make_tuple(n, k, L);
+  {
+    std::lock_guard<std::mutex> lk(g_axis_mu);
+    auto it = g_axis_cache.find(key);
+    if (it != g_axis_cache.end()) return it->second;
+  }
+  auto ax = std::make_shared<const Axis1D>(build_axis(n, k, L));
+  std::lock_guard<std::mutex> lk(g_axis_mu);
+  g_axis_cache[key] = ax;
+  return ax;
+}
+
+}  // namespace
+
+struct sem3d_plan {
+  int device = 0;
+  int num_sms = 0;
+  Geom g{};
+  int k = 0;
+  double L[3] = {0, 0, 0};
+  std::shared_ptr<const Axis1D> ax[3];
+  DevAxis dev[3];
+  sem3d_precision prec = SEM3D_FP64;
+  int sweeps = 1;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  int* d_err = nullptr;
+  std::vector<void*> owned;  // device allocations made at setup
+};
+
+namespace {
+
+template <class T>
+sem3d_status dev_upload(sem3d_plan* p, T** dst, const T* src, size_t count) {
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(setup)");
+  p->owned.push_back(d);
+  e = cudaMemcpy(d, src, count * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(setup)");
+  *dst = static_cast<T*>(d);
+  return SEM3D_OK;
+}
+
+// Split W (n x n row-major FP64) into bf16 hi + lo with row pitch Kp.
+void split_matrix(const std::vector<double>& W, int n, int Kp, std::vector<__nv_bfloat16>& hi,
+                  std::vector<__nv_bfloat16>& lo) {
+  hi.assign((size_t)n * Kp, __float2bfloat16_rn(0.f));
+  lo.assign((size_t)n * Kp, __float2bfloat16_rn(0.f));
+  for (int o = 0; o < n; ++o)
+    for (int t = 0; t < n; ++t) {
+      const float x = (float)W[(size_t)o * n + t];
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      hi[(size_t)o * Kp + t] = h;
+      lo[(size_t)o * Kp + t] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Workspace layout per mode.
+//   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
+//   BF16X3 : two split arrays {hi, lo} of Px*ny*nz bf16 each.
+size_t workspace_bytes(const sem3d_plan* p) {
+  const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
+  if (p->prec == SEM3D_FP64) return 3 * align256(N * sizeof(double));
+  const size_t Ns = (size_t)p->g.Px * p->g.ny * p->g.nz;
+  return 4 * align256(Ns * sizeof(__nv_bfloat16));
+}
+
+sem3d_status ensure_workspace(sem3d_plan* p) {
+  const size_t need = workspace_bytes(p);
+  if (p->ws && p->ws_bytes >= need) return SEM3D_OK;
+  if (p->ws && !p->ws_owned) return fail(SEM3D_ERR_INVALID_ARG, "caller workspace smaller than sem3d_workspace_size");
+  if (p->ws) { cudaFree(p->ws); p->ws = nullptr; p->ws_bytes = 0; }
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, need);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+  p->ws = d;
+  p->ws_bytes = need;
+  p->ws_owned = true;
+  return SEM3D_OK;
+}
+
+
+// ---- FP64 path: one solve of (c + H (+) H (+) H) out = in, paper order z, y, x.
+sem3d_status solve_once_f64(sem3d_plan* p, const double* in, double* out, bool accumulate, cudaStream_t s) {
+  const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
+  double* A = static_cast<double*>(p->ws);
+  double* B = reinterpret_cast<double*>(static_cast<char*>(p->ws) + align256(N * sizeof(double)));
+  const Geom& g = p->g;
+  const DevAxis* d = p->dev;
+  CUDA_TRY(launch_mode_product_f64(g, 2, d[2].Tinv, in, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  CUDA_TRY(launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  CUDA_TRY(launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_DIV, d[0].lam, d[1].lam, d[2].lam, s));
+  CUDA_TRY(launch_mode_product_f64(g, 2, d[2].T, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  CUDA_TRY(launch_mode_product_f64(g, 1, d[1].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  CUDA_TRY(launch_mode_product_f64(g, 0, d[0].T, A, out, accumulate ? EPI_ACCUM : EPI_STORE, nullptr, nullptr,
+                                   nullptr, s));
+  return SEM3D_OK;
+}
+
+// ---- BF16x3 path: the split input is in buffer S0; result into FP64 out.
+sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double* out, bool accumulate,
+                               cudaStream_t s) {
+  const Geom& g = p->g;
+  const DevAxis* d = p->dev;
+  const float *lx = d[0].lamf, *ly = d[1].lamf, *lz = d[2].lamf;
+  const int sms = p->num_sms;
+  int* e = p->d_err;
+  CUDA_TRY(launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  CUDA_TRY(launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  CUDA_TRY(launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
+  CUDA_TRY(launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  CUDA_TRY(launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  CUDA_TRY(launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, out, accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz,
+                                      e, sms, s));
+  return SEM3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sem3d_last_error(void) { return g_last_error.c_str(); }
+
+sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, double Lz, double c,
+                         sem3d_handle* out) {
+  if (!out) return fail(SEM3D_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || k > 24) return fail(SEM3D_ERR_INVALID_ARG, "k must be in [1, 24]");
+  const int n3[3] = {nx, ny, nz};
+  const double L3[3] = {Lx, Ly, Lz};
+  for (int a = 0; a < 3; ++a) {
+    if (n3[a] < 1 || (n3[a] + 1) % k != 0)
+      return fail(SEM3D_ERR_INVALID_ARG, "each n must be >= 1 with (n+1) % k == 0");
+    if (!(L3[a] > 0.0) || !std::isfinite(L3[a])) return fail(SEM3D_ERR_INVALID_ARG, "box lengths must be > 0");
+  }
+  if ((double)nx * ny * nz >= 1099511627776.0) return fail(SEM3D_ERR_INVALID_ARG, "grid too large");
+  if (!std::isfinite(c)) return fail(SEM3D_ERR_INVALID_ARG, "c must be finite");
+  std::unique_ptr<sem3d_plan> p(new (std::nothrow) sem3d_plan());
+  if (!p) return fail(SEM3D_ERR_OOM, "host allocation failed");
+  try {
+    for (int a = 0; a < 3; ++a) p->ax[a] = get_axis(n3[a], k, L3[a]);
+  } catch (const std::exception& ex) {
+    return fail(SEM3D_ERR_INVALID_ARG, std::string("axis setup failed: ") + ex.what());
+  }
+  const double lmin = p->ax[0]->lam[0] + p->ax[1]->lam[0] + p->ax[2]->lam[0];
+  if (!(c > -lmin)) return fail(SEM3D_ERR_INVALID_ARG, "c <= -(lambda_x1 + lambda_y1 + lambda_z1): not definite");
+  CUDA_TRY(cudaGetDevice(&p->device));
+  CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+  p->g.nx = nx; p->g.ny = ny; p->g.nz = nz; p->g.Px = pad8(nx); p->g.c = c;
+  p->k = k;
+  for (int a = 0; a < 3; ++a) p->L[a] = L3[a];
+  for (int a = 0; a < 3; ++a) {
+    const Axis1D& A = *p->ax[a];
+    DevAxis& D = p->dev[a];
+    D.n = A.n; D.k = k; D.Kp = pad8(A.n);
+    sem3d_status st;
+    if ((st = dev_upload(p.get(), &D.T, A.T.data(), A.T.size())) != SEM3D_OK) return st;
+    if ((st = dev_upload(p.get(), &D.Tinv, A.Tinv.data(), A.Tinv.size())) != SEM3D_OK) return st;
+    if ((st = dev_upload(p.get(), &D.lam, A.lam.data(), A.lam.size())) != SEM3D_OK) return st;
+    std::vector<float> lf(A.lam.begin(), A.lam.end());
+    if ((st = dev_upload(p.get(), &D.lamf, lf.data(), lf.size())) != SEM3D_OK) return st;
+    if ((st = dev_upload(p.get(), &D.Hband, A.Hband.data(), A.Hband.size())) != SEM3D_OK) return st;
+    if ((st = dev_upload(p.get(), &D.band_lo, A.band_lo.data(), A.band_lo.size())) != SEM3D_OK) return st;
+    if ((st = dev_upload(p.get(), &D.band_hi, A.band_hi.data(), A.band_hi.size())) != SEM3D_OK) return st;
+    std::vector<__nv_bfloat16> hi, lo;
+    for (int w = 0; w < 2; ++w) {
+      split_matrix(w == 0 ? A.Tinv : A.T, A.n, D.Kp, hi, lo);
+      if ((st = dev_upload(p.get(), &D.W_hi[w], hi.data(), hi.size())) != SEM3D_OK) return st;
+      if ((st = dev_upload(p.get(), &D.W_lo[w], lo.data(), lo.size())) != SEM3D_OK) return st;
+    }
+  }
+  {
+    void* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, 256));
+    p->owned.push_back(d);
+    CUDA_TRY(cudaMemset(d, 0, 256));
+    p->d_err = static_cast<int*>(d);
+  }
+  *out = p.release();
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweeps) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  if (prec != SEM3D_FP64 && prec != SEM3D_BF16X3) return fail(SEM3D_ERR_INVALID_ARG, "unknown precision");
+  if (sweeps < 0 || sweeps > 16) return fail(SEM3D_ERR_INVALID_ARG, "sweeps must be in [0, 16]");
+  if (prec == SEM3D_BF16X3) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
+    if (major != 10 || minor != 3) return fail(SEM3D_ERR_UNSUPPORTED, "BF16X3 needs an sm_103 GPU");
+  }
+  h->prec = prec;
+  h->sweeps = sweeps;
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_workspace_size(sem3d_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  *bytes = workspace_bytes(h);
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_set_workspace(sem3d_handle h, void* dptr, size_t bytes) {
+  if (!h || !dptr) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(dptr) & 255) != 0) return fail(SEM3D_ERR_INVALID_ARG, "workspace not 256-B aligned");
+  if (bytes < workspace_bytes(h)) return fail(SEM3D_ERR_INVALID_ARG, "workspace too small");
+  if (h->ws && h->ws_owned) cudaFree(h->ws);
+  h->ws = dptr;
+  h->ws_bytes = bytes;
+  h->ws_owned = false;
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* stream) {
+  if (!h || !f || !u) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  if (f == u || (f < u + N && u < f + N)) return fail(SEM3D_ERR_INVALID_ARG, "f and u overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sem3d_status st = ensure_workspace(h);
+  if (st != SEM3D_OK) return st;
+  if (h->prec == SEM3D_FP64) {
+    double* r = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(N * sizeof(double)));
+    if ((st = solve_once_f64(h, f, u, false, s)) != SEM3D_OK) return st;
+    for (int sw = 0; sw < h->sweeps; ++sw) {
+      CUDA_TRY(launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+      if ((st = solve_once_f64(h, r, u, true, s)) != SEM3D_OK) return st;
+    }
+  } else {
+    const size_t Ns = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(__nv_bfloat16));
+    char* w = static_cast<char*>(h->ws);
+    TcBuffers S0{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
+    TcBuffers S1{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
+    CUDA_TRY(launch_split(h->g, f, S0.hi, S0.lo, s));
+    if ((st = solve_once_bf16x3(h, S0, S1, u, false, s)) != SEM3D_OK) return st;
+    for (int sw = 0; sw < h->sweeps; ++sw) {
+      CUDA_TRY(launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
+      if ((st = solve_once_bf16x3(h, S0, S1, u, true, s)) != SEM3D_OK) return st;
+    }
+  }
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_apply(sem3d_handle h, const double* u, double* Au, void* stream) {
+  if (!h || !u || !Au) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  if (u < Au + N && Au < u + N) return fail(SEM3D_ERR_INVALID_ARG, "u and Au overlap");
+  CUDA_TRY(launch_stencil(h->g, h->k, h->dev, u, nullptr, Au, nullptr, nullptr, 0, static_cast<cudaStream_t>(stream)));
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_get_nodes(sem3d_handle h, int axis, double* x_host) {
+  if (!h || !x_host || axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
+  std::memcpy(x_host, h->ax[axis]->x.data(), h->ax[axis]->x.size() * sizeof(double));
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_get_eigs(sem3d_handle h, int axis, double* lambda_host, double* T_host) {
+  if (!h || axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
+  const Axis1D& A = *h->ax[axis];
+  if (lambda_host) std::memcpy(lambda_host, A.lam.data(), A.lam.size() * sizeof(double));
+  if (T_host) {
+    const int n = A.n;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) T_host[(size_t)j * n + i] = A.T[(size_t)i * n + j];  // column-major
+  }
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_axis_info(int n, int k, double L, double* x, double* M, double* lambda, double* T) {
+  if (k < 1 || k > 24 || n < 1 || (n + 1) % k != 0 || !(L > 0.0))
+    return fail(SEM3D_ERR_INVALID_ARG, "need k in [1,24], n >= 1, (n+1) % k == 0, L > 0");
+  std::shared_ptr<const Axis1D> ax;
+  try {
+    ax = get_axis(n, k, L);
+  } catch (const std::exception& ex) {
+    return fail(SEM3D_ERR_INVALID_ARG, std::string("axis setup failed: ") + ex.what());
+  }
+  if (x) std::memcpy(x, ax->x.data(), n * sizeof(double));
+  if (M) std::memcpy(M, ax->M.data(), n * sizeof(double));
+  if (lambda) std::memcpy(lambda, ax->lam.data(), n * sizeof(double));
+  if (T)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) T[(size_t)j * n + i] = ax->T[(size_t)i * n + j];
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_sync_check(sem3d_handle h, void* stream) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int flags = 0;
+  CUDA_TRY(cudaMemcpy(&flags, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flags != 0) {
+    CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (flags & (1 << SEM3D_ERR_TIMEOUT)) return fail(SEM3D_ERR_TIMEOUT, "a tensor-core kernel's bounded wait expired");
+    return fail(SEM3D_ERR_CUDA, "device error flag set");
+  }
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_destroy(sem3d_handle h) {
+  if (!h) return SEM3D_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (h->ws && h->ws_owned) cudaFree(h->ws);
+  for (void* d : h->owned) cudaFree(d);
+  delete h;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(destroy)");
+  return SEM3D_OK;
+}
+
+}  // extern "C"

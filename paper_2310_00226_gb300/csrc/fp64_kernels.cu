@@ -1,0 +1,281 @@
+// FP64 kernels: the plain-FP64 mode product (mma.sync DMMA), the banded
+// FP64 operator / residual, and the FP64 -> split-bf16 conversion.
+#include "sem3d_internal.h"
+
+namespace sem3d {
+
+namespace {
+
+// ------------------------------------------------------------------ DMMA GEMM
+//
+// A mode product along one axis is a GEMM C[row, o] = sum_t A[row, t] W[o, t]
+// where `row` enumerates the grid lines along that axis.  Rows are described
+// by two loops (p < R1 with stride s1, q < R2 with stride s2) and the axis
+// index has stride sm, so the same kernel serves x, y and z without
+// transposes (Section 2.4, Eq. 11: the paper's tensorprod / pagemtimes).
+//
+// CTA tile: 64 rows x 64 outputs, K chunk 16; 8 warps, each owning 32 rows x
+// 16 outputs = 4 x 2 fragments of mma.m8n8k4.f64.
+
+constexpr int F64_BM = 64, F64_BN = 64, F64_BK = 16;
+
+struct F64Pass {
+  const double* in;
+  double* out;
+  const double* W;        // n x n row-major
+  long long s1, s2, sm;   // strides of p, q and the axis index
+  int R1, R2, n;          // row loops and axis length
+  int epi;
+  int nx, ny;             // to decode (i, j, l) for the division epilogue
+  const double *lamx, *lamy, *lamz;
+  double c;
+};
+
+template <bool KCONTIG>
+__global__ void __launch_bounds__(256) mode_product_f64_kernel(F64Pass p) {
+  __shared__ double As[F64_BK][F64_BM + 1];
+  __shared__ double Bs[F64_BK][F64_BN + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long rows = (long long)p.R1 * p.R2;
+  const long long row0 = (long long)blockIdx.x * F64_BM;
+  const int o0 = blockIdx.y * F64_BN;
+  const int wr = (warp & 1) * 32, wc = (warp >> 1) * 16;
+
+  double acc[4][2][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+
+  for (int t0 = 0; t0 < p.n; t0 += F64_BK) {
+    // A tile: 64 rows x 16 t.
+#pragma unroll
+    for (int it = 0; it < (F64_BM * F64_BK) / 256; ++it) {
+      const int e = tid + it * 256;
+      int r, kk;
+      if (KCONTIG) { kk = e % F64_BK; r = e / F64_BK; }
+      else { r = e % F64_BM; kk = e / F64_BM; }
+      const long long row = row0 + r;
+      const int t = t0 + kk;
+      double v = 0.0;
+      if (row < rows && t < p.n) {
+        const long long pp = row % p.R1, qq = row / p.R1;
+        v = p.in[pp * p.s1 + qq * p.s2 + (long long)t * p.sm];
+      }
+      As[kk][r] = v;
+    }
+    // W tile: 64 outputs x 16 t (row-major W, t contiguous).
+#pragma unroll
+    for (int it = 0; it < (F64_BN * F64_BK) / 256; ++it) {
+      const int e = tid + it * 256;
+      const int kk = e % F64_BK, o = e / F64_BK;
+      const int oo = o0 + o, t = t0 + kk;
+      Bs[kk][o] = (oo < p.n && t < p.n) ? p.W[(long long)oo * p.n + t] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k4 = 0; k4 < F64_BK; k4 += 4) {
+      double afr[4], bfr[2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) afr[a] = As[k4 + (lane & 3)][wr + a * 8 + (lane >> 2)];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) bfr[b] = Bs[k4 + (lane & 3)][wc + b * 8 + (lane >> 2)];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+          asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                       : "+d"(acc[a][b][0]), "+d"(acc[a][b][1])
+                       : "d"(afr[a]), "d"(bfr[b]));
+    }
+    __syncthreads();
+  }
+  // Epilogue: fragment (a, b) holds rows wr + a*8 + lane/4, outputs
+  // wc + b*8 + 2*(lane%4) + {0,1}.
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const long long row = row0 + wr + a * 8 + (lane >> 2);
+    if (row >= rows) continue;
+    const long long pp = row % p.R1, qq = row / p.R1;
+    const long long base = pp * p.s1 + qq * p.s2;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o = o0 + wc + b * 8 + 2 * (lane & 3) + h;
+        if (o >= p.n) continue;
+        const long long idx = base + (long long)o * p.sm;
+        double v = acc[a][b][h];
+        if (p.epi == EPI_DIV) {
+          const long long i = idx % p.nx, jl = idx / p.nx;
+          const long long j = jl % p.ny, l = jl / p.ny;
+          v = v / (p.lamx[i] + p.lamy[j] + p.lamz[l] + p.c);
+          p.out[idx] = v;
+        } else if (p.epi == EPI_ACCUM) {
+          p.out[idx] += v;
+        } else {
+          p.out[idx] = v;
+        }
+      }
+  }
+}
+
+// ------------------------------------------------------------------ stencil
+//
+// (H_x (+) H_y (+) H_z) u with the banded H = M^{-1} S of each axis
+// (Eq. 12): row i of H couples the nodes of the one or two elements that
+// contain node i, stored as H[i][i+d], d in [-k, k].  One thread per node.
+
+struct StencilArgs {
+  const double* u;
+  const double* f;
+  double* out64;
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  const double *Hx, *Hy, *Hz;
+  const int *lox, *hix, *loy, *hiy, *loz, *hiz;
+  int nx, ny, nz, k, Px, mode;
+  double c;
+};
+
+__global__ void __launch_bounds__(256) stencil_kernel(StencilArgs a) {
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  const int bw = 2 * a.k + 1;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % a.nx);
+    const long long jl = idx / a.nx;
+    const int j = (int)(jl % a.ny), l = (int)(jl / a.ny);
+    const double* u = a.u;
+    double s = a.c * u[idx];
+    // x: the band of row i (lanes of a warp sit on different rows of H_x).
+    {
+      const double* h = a.Hx + (long long)i * bw;
+      const long long base = idx - i;
+      for (int t = a.lox[i]; t <= a.hix[i]; ++t) s += h[t - i + a.k] * u[base + t];
+    }
+    // y
+    {
+      const double* h = a.Hy + (long long)j * bw;
+      const long long base = idx - (long long)j * a.nx;
+      for (int t = a.loy[j]; t <= a.hiy[j]; ++t) s += h[t - j + a.k] * u[base + (long long)t * a.nx];
+    }
+    // z
+    {
+      const double* h = a.Hz + (long long)l * bw;
+      const long long pl = (long long)a.nx * a.ny;
+      const long long base = idx - (long long)l * pl;
+      for (int t = a.loz[l]; t <= a.hiz[l]; ++t) s += h[t - l + a.k] * u[base + (long long)t * pl];
+    }
+    if (a.mode == 0) {
+      a.out64[idx] = s;
+    } else {
+      const double r = a.f[idx] - s;
+      if (a.mode == 1) {
+        a.out64[idx] = r;
+      } else {
+        const float rf = (float)r;
+        const __nv_bfloat16 h16 = __float2bfloat16_rn(rf);
+        const __nv_bfloat16 l16 = __float2bfloat16_rn(rf - __bfloat162float(h16));
+        const long long o = (long long)i + (long long)a.Px * jl;
+        a.hi[o] = h16;
+        a.lo[o] = l16;
+      }
+    }
+  }
+}
+
+// Zero the pad columns i in [nx, Px) of a split array (the stencil writes
+// only i < nx).
+__global__ void zero_pads_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int nx, int Px, long long lines) {
+  const int w = Px - nx;
+  const long long total = lines * w;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long line = e / w;
+    const long long o = line * Px + nx + (e % w);
+    hi[o] = __float2bfloat16_rn(0.f);
+    lo[o] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// FP64 (dense, pitch nx) -> bf16 hi + lo (pitch Px, zero pads):
+// hi = bf16(x), lo = bf16(x - hi), x rounded to FP32 first.
+__global__ void __launch_bounds__(256) split_kernel(const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, int nx,
+                                                    int Px, long long lines) {
+  const long long total = lines * Px;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long line = e / Px;
+    const int i = (int)(e - line * Px);
+    float x = 0.f;
+    if (i < nx) x = (float)in[line * nx + i];
+    const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
+    hi[e] = h16;
+    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h16));
+  }
+}
+
+int grid_for(long long work, int per_block) {
+  long long b = (work + per_block - 1) / per_block;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_mode_product_f64(const Geom& g, int axis, const double* W, const double* in, double* out, int epi,
+                                    const double* lamx, const double* lamy, const double* lamz, cudaStream_t s) {
+  F64Pass p{};
+  p.in = in;
+  p.out = out;
+  p.W = W;
+  p.epi = epi;
+  p.nx = g.nx;
+  p.ny = g.ny;
+  p.lamx = lamx;
+  p.lamy = lamy;
+  p.lamz = lamz;
+  p.c = g.c;
+  const long long nxy = (long long)g.nx * g.ny;
+  bool kcontig = false;
+  if (axis == 0) {         // rows = (j,l) lines, t = i contiguous
+    p.R1 = g.ny * g.nz; p.R2 = 1; p.s1 = g.nx; p.s2 = 0; p.sm = 1; p.n = g.nx; kcontig = true;
+  } else if (axis == 1) {  // rows = (i, l), t = j
+    p.R1 = g.nx; p.R2 = g.nz; p.s1 = 1; p.s2 = nxy; p.sm = g.nx; p.n = g.ny;
+  } else {                 // rows = (i,j) plane, t = l
+    p.R1 = (int)nxy; p.R2 = 1; p.s1 = 1; p.s2 = 0; p.sm = nxy; p.n = g.nz;
+  }
+  const long long rows = (long long)p.R1 * p.R2;
+  dim3 grid((unsigned)((rows + F64_BM - 1) / F64_BM), (unsigned)((p.n + F64_BN - 1) / F64_BN));
+  if (kcontig) mode_product_f64_kernel<true><<<grid, 256, 0, s>>>(p);
+  else mode_product_f64_kernel<false><<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f, double* out64,
+                           __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int mode, cudaStream_t s) {
+  StencilArgs a{};
+  a.u = u; a.f = f; a.out64 = out64; a.hi = out_hi; a.lo = out_lo;
+  a.Hx = ax[0].Hband; a.Hy = ax[1].Hband; a.Hz = ax[2].Hband;
+  a.lox = ax[0].band_lo; a.hix = ax[0].band_hi;
+  a.loy = ax[1].band_lo; a.hiy = ax[1].band_hi;
+  a.loz = ax[2].band_lo; a.hiz = ax[2].band_hi;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.k = k; a.Px = g.Px; a.mode = mode; a.c = g.c;
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  stencil_kernel<<<grid_for(N, 256), 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || mode != 2 || g.Px == g.nx) return e;
+  const long long lines = (long long)g.ny * g.nz;
+  zero_pads_kernel<<<grid_for(lines * (g.Px - g.nx), 256), 256, 0, s>>>(out_hi, out_lo, g.nx, g.Px, lines);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+  const long long lines = (long long)g.ny * g.nz;
+  split_kernel<<<grid_for(lines * g.Px, 256), 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines);
+  return cudaGetLastError();
+}
+
+}  // namespace sem3d

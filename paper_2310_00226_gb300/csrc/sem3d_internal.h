@@ -1,0 +1,97 @@
+// Internal declarations of libsem3d (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sem3d.h"
+
+namespace sem3d {
+
+// ---------------------------------------------------------------- host setup
+
+// 1D data of one axis: n interior nodes of degree k on [0, L], Ne = (n+1)/k.
+struct Axis1D {
+  int n = 0, k = 0, Ne = 0;
+  double L = 0.0;
+  std::vector<double> x;        // interior node coordinates
+  std::vector<double> M;        // lumped mass diagonal
+  std::vector<double> S;        // stiffness, n x n row-major
+  std::vector<double> lam;      // eigenvalues of H = M^{-1} S, ascending
+  std::vector<double> T;        // n x n row-major, T[i*n+j] = component i of eigenvector j
+  std::vector<double> Tinv;     // n x n row-major, T^{-1}
+  std::vector<double> Hband;    // n x (2k+1): H[i][i+d] at [i*(2k+1) + d + k]
+  std::vector<int> band_lo, band_hi;  // nonzero column range of row i of H
+};
+
+void gll_rule(int N, std::vector<double>& r, std::vector<double>& w);
+void gll_diff(int N, const std::vector<double>& r, std::vector<double>& D);
+Axis1D build_axis(int n, int k, double L);
+
+// ---------------------------------------------------------------- device data
+
+// Pitch (elements) of the x dimension of the tensor-core working arrays:
+// a multiple of 8 so that every bf16 row starts on a 16-byte boundary (TMA).
+inline int pad8(int n) { return (n + 7) & ~7; }
+
+struct DevAxis {
+  int n = 0, k = 0, Kp = 0;     // Kp = pad8(n): row pitch of the bf16 matrices
+  double* T = nullptr;          // FP64 n x n row-major (W[out][in] for the backward pass)
+  double* Tinv = nullptr;       // FP64 n x n row-major (W[out][in] for the forward pass)
+  double* lam = nullptr;        // FP64 eigenvalues
+  float* lamf = nullptr;        // FP32 copy for the low-precision epilogues
+  double* Hband = nullptr;      // FP64 n x (2k+1)
+  int* band_lo = nullptr;
+  int* band_hi = nullptr;
+  __nv_bfloat16* W_hi[2] = {nullptr, nullptr};  // [0] = T^{-1}, [1] = T; n rows x Kp
+  __nv_bfloat16* W_lo[2] = {nullptr, nullptr};
+};
+
+// Epilogues of a mode-product pass.
+enum Epi : int {
+  EPI_STORE = 0,       // out = acc
+  EPI_DIV = 1,         // out = acc / (lam_x,i + lam_y,j + lam_z,l + c)
+  EPI_ACCUM = 2        // out += acc (FP64 outputs only)
+};
+
+// Grid geometry of one solve.
+struct Geom {
+  int nx, ny, nz;
+  int Px;              // pitch of x in the bf16 working arrays
+  double c;
+};
+
+// ---- FP64 kernels (fp64_kernels.cu)
+// One mode product along `axis` (0 = x, 1 = y, 2 = z) on dense n-pitch FP64
+// arrays: out[.., o, ..] (=|+=|/=) sum_t W[o*n + t] * in[.., t, ..].
+cudaError_t launch_mode_product_f64(const Geom& g, int axis, const double* W, const double* in, double* out,
+                                    int epi, const double* lamx, const double* lamy, const double* lamz,
+                                    cudaStream_t s);
+// Au = c u + (H_x (+) H_y (+) H_z) u            (mode 0)
+// r  = f - c u - (H_x (+) H_y (+) H_z) u        (mode 1, FP64 r)
+// r  = same, written as bf16 hi/lo at pitch Px   (mode 2)
+cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f, double* out64,
+                           __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int mode, cudaStream_t s);
+// FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads.
+cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+
+// ---- tcgen05 kernels (tc_kernels.cu)
+struct TcBuffers {
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+};
+// Tensor maps and launch data of one BF16x3 mode product, prepared on the host.
+struct TcPassPlan;
+// One BF16x3 mode product along `axis` reading the split array `in` and
+// writing either the split array `out` (EPI_STORE / EPI_DIV) or the FP64
+// dense n-pitch array out64 (EPI_STORE / EPI_ACCUM).
+cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
+                                       TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
+                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s);
+
+}  // namespace sem3d

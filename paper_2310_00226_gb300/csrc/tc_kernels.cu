@@ -1,0 +1,542 @@
+// tcgen05 tensor-core mode product in split-bf16 arithmetic (BF16x3).
+//
+// One mode product of the solve (Section 2.4, Eq. 13: the tensorprod /
+// pagemtimes steps) is a GEMM  D[row, o] = sum_t A[row, t] * W[o, t]  where
+// `row` enumerates the grid lines along the contracted axis, t runs along the
+// axis and W is T^{-1} (forward) or T (backward).  Operands are split into two
+// bfloat16 numbers, x = x_hi + x_lo, and the product is accumulated in FP32
+// tensor memory as A_hi W_hi + A_hi W_lo + A_lo W_hi (the dropped lo*lo term
+// is below FP32 rounding of the sum).
+//
+// Layout (bf16 working arrays, x pitch Px = pad8(nx), element (i,j,l) at
+// i + Px*(j + ny*l)):
+//   x pass: rows = (j,l) lines, t = i is contiguous      -> A is K-major
+//   y pass: rows = i (contiguous), t = j, batch = l      -> A is MN-major
+//   z pass: rows = i + Px*j (contiguous), t = l           -> A is MN-major
+// TMA tensor maps stride along the contracted axis directly, so no pass ever
+// transposes data.  TMEM lane = row, so for y and z the epilogue stores of a
+// warp are 32 consecutive addresses.
+//
+// Kernel structure (one CTA per SM, persistent over output tiles of
+// 128 rows x 256 outputs):
+//   warp 0      : TMA producer (one thread)
+//   warp 1      : TMEM allocator + MMA issuer (one thread)
+//   warps 2..5  : epilogue (TMEM -> registers -> global), 128 threads
+// Shared memory holds STAGES stages of {A_hi, A_lo, W_hi, W_lo} K-slices of 64;
+// TMEM holds two 128 x 256 FP32 accumulators so the epilogue of one tile
+// overlaps the MMAs of the next.  Every wait is bounded: on expiry the kernel
+// records SEM3D_ERR_TIMEOUT in *err, drains its own copies and MMAs, frees
+// TMEM and returns.
+#include "sem3d_internal.h"
+
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace sem3d {
+
+namespace {
+
+constexpr int BM = 128;           // tile rows = TMEM lanes
+constexpr int BN = 256;           // tile outputs = TMEM columns per accumulator
+constexpr int BK = 64;            // K per stage: one 128-byte swizzle row of bf16
+constexpr int STAGES = 2;
+constexpr int A_TILE_BYTES = BM * BK * 2;  // 16 KB
+constexpr int B_TILE_BYTES = BN * BK * 2;  // 32 KB
+constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 2 * BN;  // 512
+constexpr int NUM_THREADS = 192;
+constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s per wait
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false when the wait expires
+// (recording SEM3D_ERR_TIMEOUT in *err) or, while err is non-null, when
+// another thread of the grid has already recorded an error.  err == nullptr
+// is used by the final drains: they only bound the wait.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (err != nullptr && *reinterpret_cast<volatile int*>(err) != 0) return false;
+      if (globaltimer() - t0 > WAIT_NS) {
+        if (err != nullptr) atomicOr(err, 1 << SEM3D_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (>>4), fixed version 1 at bit 46, 128-byte swizzle
+// (layout code 2 at bits 61-63).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B bf16 (bits 7-9 = 1, 10-12 = 1), A major-ness at bit 15 (1 = MN-major),
+// B K-major, N>>3 at bits 17-22, M>>4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(int m, int n, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// ---------------------------------------------------------------- kernel
+
+struct TcArgs {
+  int pass;            // 0 = x, 1 = y, 2 = z
+  int epi;             // EPI_STORE / EPI_DIV / EPI_ACCUM
+  int out_f64;         // 1: write FP64 dense n-pitch output
+  int m_tiles, n_tiles, batches, k_blocks;
+  int rows;            // valid tile rows per batch (x: ny*nz, y: Px, z: Px*ny)
+  int nout;            // valid outputs (length of the output axis)
+  int nx, ny, nz, Px;
+  __nv_bfloat16* out_hi;
+  __nv_bfloat16* out_lo;
+  double* out64;
+  const float *lamx, *lamy, *lamz;
+  float c;
+  int* err;
+};
+
+// Split an FP32 value into bf16 hi + lo.
+__device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32]) {
+  if (a.pass == 0) {
+    // row = (j,l) line, columns = output i (contiguous in memory).
+    if (row >= a.rows) return;
+    if (a.epi == EPI_DIV) {
+      const int j = row % a.ny, l = row / a.ny;
+      const float s = a.lamy[j] + a.lamz[l] + a.c;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int o = col0 + q;
+        const float d = (o < a.nout) ? __ldg(a.lamx + o) + s : 1.0f;
+        v[q] = v[q] / d;
+      }
+    }
+    if (a.out_f64) {
+      double* dst = a.out64 + (long long)row * a.nx;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int o = col0 + q;
+        if (o < a.nout) {
+          if (a.epi == EPI_ACCUM) dst[o] += (double)v[q];
+          else dst[o] = (double)v[q];
+        }
+      }
+    } else {
+      __nv_bfloat16* dh = a.out_hi + (long long)row * a.Px;
+      __nv_bfloat16* dl = a.out_lo + (long long)row * a.Px;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int o = col0 + 8 * g;
+        if (o + 8 > a.Px) break;  // Px is a multiple of 8
+        __align__(16) __nv_bfloat16 hh[8], ll[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) split2(v[8 * g + q], hh[q], ll[q]);
+        *reinterpret_cast<uint4*>(dh + o) = *reinterpret_cast<const uint4*>(hh);
+        *reinterpret_cast<uint4*>(dl + o) = *reinterpret_cast<const uint4*>(ll);
+      }
+    }
+    return;
+  }
+  // y and z passes: row = contiguous index, columns = output mode (stride).
+  if (row >= a.rows) return;
+  int i, j, l_fixed = 0;
+  long long rowoff, colstride;
+  if (a.pass == 1) {  // row = i, column = j (= b), batch = l
+    i = row; j = 0; l_fixed = batch;
+    rowoff = (long long)row + (long long)a.Px * a.ny * batch;
+    colstride = a.Px;
+  } else {            // row = i + Px*j, column = l
+    i = row % a.Px; j = row / a.Px;
+    rowoff = row;
+    colstride = (long long)a.Px * a.ny;
+  }
+  if (a.epi == EPI_DIV) {
+    const float li = __ldg(a.lamx + (i < a.nx ? i : 0));
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int o = col0 + q;
+      float d = 1.0f;
+      if (o < a.nout) {
+        if (a.pass == 1) d = li + __ldg(a.lamy + o) + __ldg(a.lamz + l_fixed) + a.c;
+        else d = li + __ldg(a.lamy + j) + __ldg(a.lamz + o) + a.c;
+      }
+      v[q] = v[q] / d;
+    }
+  }
+  if (a.out_f64) {
+    if (i >= a.nx) return;
+    long long base, cs;
+    if (a.pass == 1) { base = (long long)i + (long long)a.nx * a.ny * batch; cs = a.nx; }
+    else { base = (long long)i + (long long)a.nx * j; cs = (long long)a.nx * a.ny; }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int o = col0 + q;
+      if (o < a.nout) {
+        double* p = a.out64 + base + (long long)o * cs;
+        if (a.epi == EPI_ACCUM) *p += (double)v[q];
+        else *p = (double)v[q];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int o = col0 + q;
+      if (o < a.nout) {
+        __nv_bfloat16 h, l;
+        split2(v[q], h, l);
+        const long long off = rowoff + (long long)o * colstride;
+        a.out_hi[off] = h;
+        a.out_lo[off] = l;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                               const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+                               const TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain[1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool a_mn = (a.pass != 0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), 4); }
+    mbar_init(drain_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+
+  const int tiles_per_batch = a.m_tiles * a.n_tiles;
+  const int total_tiles = tiles_per_batch * a.batches;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+      const int b = t / tiles_per_batch;
+      const int rem = t - b * tiles_per_batch;
+      const int mt = rem / a.n_tiles, nt = rem - mt * a.n_tiles;
+      const int m0 = mt * BM, n0 = nt * BN;
+      for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t par = ((it / STAGES) & 1) ^ 1;
+        if (!mbar_wait(empty_bar(s), par, a.err)) { ok = false; break; }
+        const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
+        const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
+        mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+        const int k0 = kb * BK;
+        if (a.pass == 0) {
+          tma_load_2d(a_hi, &tmA_hi, full_bar(s), k0, m0);
+          tma_load_2d(a_lo, &tmA_lo, full_bar(s), k0, m0);
+        } else if (a.pass == 1) {
+          tma_load_3d(a_hi, &tmA_hi, full_bar(s), m0, k0, b);
+          tma_load_3d(a_hi + A_TILE_BYTES / 2, &tmA_hi, full_bar(s), m0 + 64, k0, b);
+          tma_load_3d(a_lo, &tmA_lo, full_bar(s), m0, k0, b);
+          tma_load_3d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0, b);
+        } else {
+          tma_load_2d(a_hi, &tmA_hi, full_bar(s), m0, k0);
+          tma_load_2d(a_hi + A_TILE_BYTES / 2, &tmA_hi, full_bar(s), m0 + 64, k0);
+          tma_load_2d(a_lo, &tmA_lo, full_bar(s), m0, k0);
+          tma_load_2d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0);
+        }
+        tma_load_2d(b_hi, &tmB_hi, full_bar(s), k0, n0);
+        tma_load_2d(b_lo, &tmB_lo, full_bar(s), k0, n0);
+      }
+    }
+    // Drain: every stage this thread armed must have landed before exit.
+    const int armed = it;
+    for (int q = (armed > STAGES ? armed - STAGES : 0); q < armed; ++q)
+      mbar_wait(full_bar(q % STAGES), (q / STAGES) & 1, nullptr);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer
+    constexpr uint32_t idesc_k = make_idesc(BM, BN, false);
+    constexpr uint32_t idesc_mn = make_idesc(BM, BN, true);
+    const uint32_t idesc = a_mn ? idesc_mn : idesc_k;
+    // A: K-major -> SBO 1024 (8-row groups), advance 32 B per K=16.
+    //    MN-major -> LBO 8192 (next 64-row block), SBO 1024 (next 8 K rows),
+    //    advance 2048 B per K=16.
+    const uint32_t a_lbo = a_mn ? 8192u : 16u, a_sbo = 1024u, a_kstep = a_mn ? 2048u : 32u;
+    int it = 0, tl = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      if (!mbar_wait(tempty_bar(buf), ((tl >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t tmem_d = tmem_base + (uint32_t)(buf * BN);
+      for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(full_bar(s), (it / STAGES) & 1, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
+        const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
+#pragma unroll
+        for (int k16 = 0; k16 < BK / 16; ++k16) {
+          const uint64_t dah = smem_desc(a_hi + k16 * a_kstep, a_lbo, a_sbo);
+          const uint64_t dal = smem_desc(a_lo + k16 * a_kstep, a_lbo, a_sbo);
+          const uint64_t dbh = smem_desc(b_hi + k16 * 32u, 16u, 1024u);
+          const uint64_t dbl = smem_desc(b_lo + k16 * 32u, 16u, 1024u);
+          const uint32_t acc = (kb | k16) ? 1u : 0u;
+          mma_bf16(tmem_d, dah, dbh, idesc, acc);
+          mma_bf16(tmem_d, dah, dbl, idesc, 1u);
+          mma_bf16(tmem_d, dal, dbh, idesc, 1u);
+        }
+        mma_commit(empty_bar(s));  // frees the smem stage when these MMAs finish
+      }
+      if (!ok) break;
+      mma_commit(tfull_bar(buf));  // accumulator ready for the epilogue
+    }
+    // Drain: wait for every MMA this thread issued before TMEM is freed.
+    mma_commit(drain_bar);
+    mbar_wait(drain_bar, 0, nullptr);
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue
+    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    int tl = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      if (!mbar_wait(tfull_bar(buf), (tl >> 1) & 1, a.err)) break;
+      tc_fence_after();
+      const int b = t / tiles_per_batch;
+      const int rem = t - b * tiles_per_batch;
+      const int mt = rem / a.n_tiles, nt = rem - mt * a.n_tiles;
+      const int row = mt * BM + quad * 32 + lane;
+      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        const int col0 = nt * BN + ch * 32;
+        if (col0 >= a.nout) break;  // warp-uniform
+        float v[32];
+        tmem_ld32(taddr + ch * 32, v);
+        epilogue_chunk(a, row, col0, b, v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(buf));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
+              const uint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gd[3], gs[2];
+  cuuint32_t bx[3], es[3] = {1, 1, 1};
+  for (int r = 0; r < rank; ++r) { gd[r] = dims[r]; bx[r] = box[r]; }
+  for (int r = 0; r + 1 < rank; ++r) gs[r] = strides_bytes[r];
+  CUresult res = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return res == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
+                                       TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
+                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(mode_product_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  TcArgs a{};
+  a.pass = axis;
+  a.epi = epi;
+  a.out_f64 = out64 != nullptr;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
+  a.out_hi = out.hi; a.out_lo = out.lo; a.out64 = out64;
+  a.lamx = lamx; a.lamy = lamy; a.lamz = lamz; a.c = (float)g.c;
+  a.err = err_flag;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  const uint64_t Px = (uint64_t)g.Px, ny = (uint64_t)g.ny, nz = (uint64_t)g.nz;
+  bool ok = true;
+  int nin = 0;
+  if (axis == 0) {
+    // A: dims {i: nx, line: ny*nz}, line stride Px*2 B; box {64 (K), 128 rows}
+    const uint64_t dims[2] = {(uint64_t)g.nx, ny * nz};
+    const uint64_t str[1] = {Px * 2};
+    const uint32_t box[2] = {64, 128};
+    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box) && make_map(&mAl, in.lo, 2, dims, str, box);
+    a.rows = g.ny * g.nz; a.batches = 1; nin = g.nx;
+  } else if (axis == 1) {
+    // A: dims {i: Px, j: ny, l: nz}; box {64 rows, 64 K, 1}
+    const uint64_t dims[3] = {Px, ny, nz};
+    const uint64_t str[2] = {Px * 2, Px * ny * 2};
+    const uint32_t box[3] = {64, 64, 1};
+    ok = ok && make_map(&mAh, in.hi, 3, dims, str, box) && make_map(&mAl, in.lo, 3, dims, str, box);
+    a.rows = g.Px; a.batches = g.nz; nin = g.ny;
+  } else {
+    // A: dims {m = i + Px*j: Px*ny, l: nz}; box {64 rows, 64 K}
+    const uint64_t dims[2] = {Px * ny, nz};
+    const uint64_t str[1] = {Px * ny * 2};
+    const uint32_t box[2] = {64, 64};
+    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box) && make_map(&mAl, in.lo, 2, dims, str, box);
+    a.rows = g.Px * g.ny; a.batches = 1; nin = g.nz;
+  }
+  {
+    // W: dims {t: n, o: n}, row pitch Kp*2 B; box {64 (K), 256 rows}
+    const uint64_t dims[2] = {(uint64_t)W.n, (uint64_t)W.n};
+    const uint64_t str[1] = {(uint64_t)W.Kp * 2};
+    const uint32_t box[2] = {64, (uint32_t)BN};
+    ok = ok && make_map(&mBh, W.W_hi[which], 2, dims, str, box) && make_map(&mBl, W.W_lo[which], 2, dims, str, box);
+  }
+  if (!ok) return cudaErrorInvalidValue;
+  a.nout = W.n;
+  a.m_tiles = (a.rows + BM - 1) / BM;
+  a.n_tiles = (W.n + BN - 1) / BN;
+  a.k_blocks = (nin + BK - 1) / BK;
+  const long long total = (long long)a.m_tiles * a.n_tiles * a.batches;
+  if (total >= (1LL << 31)) return cudaErrorInvalidValue;
+  const int grid = (int)(total < num_sms ? total : num_sms);
+  mode_product_bf16x3_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
+  return cudaGetLastError();
+}
+
+}  // namespace sem3d

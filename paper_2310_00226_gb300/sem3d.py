@@ -1,0 +1,180 @@
+"""Python binding of the libsem3d C ABI (include/sem3d.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts torch tensors and streams into pointers.  It never falls back to
+another implementation: if ``libsem3d.so`` is missing, loading raises.
+
+Arrays are torch tensors of dtype float64 on a CUDA device, contiguous, of
+shape (nz, ny, nx) (x fastest, the layout of the C ABI) or flat.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsem3d.so")
+
+SEM3D_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "UNSUPPORTED"}
+PRECISIONS = {"fp64": 0, "bf16x3": 5}
+
+#: Every entry point declared in include/sem3d.h.
+EXPORTS = (
+    "sem3d_setup",
+    "sem3d_set_precision",
+    "sem3d_workspace_size",
+    "sem3d_set_workspace",
+    "sem3d_solve",
+    "sem3d_apply",
+    "sem3d_get_nodes",
+    "sem3d_get_eigs",
+    "sem3d_axis_info",
+    "sem3d_sync_check",
+    "sem3d_destroy",
+    "sem3d_last_error",
+)
+
+_lib = None
+
+
+class Sem3dError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsem3d.so (built by paper_2310_00226_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libsem3d.so not found at {_LIB_PATH}; run paper_2310_00226_gb300.build.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    L.sem3d_setup.argtypes = [c_int, c_int, c_int, c_int, c_double, c_double, c_double, c_double,
+                              ctypes.POINTER(c_void_p)]
+    L.sem3d_set_precision.argtypes = [c_void_p, c_int, c_int]
+    L.sem3d_workspace_size.argtypes = [c_void_p, ctypes.POINTER(c_size_t)]
+    L.sem3d_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
+    L.sem3d_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_get_nodes.argtypes = [c_void_p, c_int, c_void_p]
+    L.sem3d_get_eigs.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
+    L.sem3d_axis_info.argtypes = [c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_sync_check.argtypes = [c_void_p, c_void_p]
+    L.sem3d_destroy.argtypes = [c_void_p]
+    L.sem3d_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "sem3d_last_error":
+            getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != SEM3D_OK:
+        raise Sem3dError(status, where, lib().sem3d_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_ptr(t, n: int, name: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return t.data_ptr()
+
+
+def axis_info(n: int, k: int, L: float = 1.0):
+    """Host-only 1D axis data as sem3d_setup builds it: (x, M, lambda, T)."""
+    x, M, lam = np.empty(n), np.empty(n), np.empty(n)
+    T = np.empty((n, n), order="F")
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().sem3d_axis_info(n, k, float(L), ptr(x), ptr(M), ptr(lam), ptr(T)), "sem3d_axis_info")
+    return x, M, lam, T
+
+
+class Plan:
+    """A libsem3d plan (sem3d_setup ... sem3d_destroy)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, k: int, L=(1.0, 1.0, 1.0), c: float = 0.0):
+        h = ctypes.c_void_p()
+        _check(lib().sem3d_setup(nx, ny, nz, k, float(L[0]), float(L[1]), float(L[2]), float(c), ctypes.byref(h)),
+               "sem3d_setup")
+        self._h = h
+        self.shape = (nz, ny, nx)
+        self.n = (nx, ny, nz)
+        self.k = k
+        self.c = c
+
+    @property
+    def numel(self) -> int:
+        nx, ny, nz = self.n
+        return nx * ny * nz
+
+    def set_precision(self, precision: str = "fp64", sweeps: int = 1):
+        _check(lib().sem3d_set_precision(self._h, PRECISIONS[precision], int(sweeps)), "sem3d_set_precision")
+
+    def workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().sem3d_workspace_size(self._h, ctypes.byref(b)), "sem3d_workspace_size")
+        return b.value
+
+    def set_workspace(self, buf):
+        _check(lib().sem3d_set_workspace(self._h, ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()),
+               "sem3d_set_workspace")
+
+    def solve(self, f, u, stream=None):
+        _check(lib().sem3d_solve(self._h, ctypes.c_void_p(_dev_ptr(f, self.numel, "f")),
+                                 ctypes.c_void_p(_dev_ptr(u, self.numel, "u")), ctypes.c_void_p(_stream_ptr(stream))),
+               "sem3d_solve")
+
+    def apply(self, u, Au, stream=None):
+        _check(lib().sem3d_apply(self._h, ctypes.c_void_p(_dev_ptr(u, self.numel, "u")),
+                                 ctypes.c_void_p(_dev_ptr(Au, self.numel, "Au")), ctypes.c_void_p(_stream_ptr(stream))),
+               "sem3d_apply")
+
+    def sync_check(self, stream=None):
+        _check(lib().sem3d_sync_check(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_sync_check")
+
+    def nodes(self, axis: int) -> np.ndarray:
+        x = np.empty(self.n[axis])
+        _check(lib().sem3d_get_nodes(self._h, axis, x.ctypes.data_as(ctypes.c_void_p)), "sem3d_get_nodes")
+        return x
+
+    def eigs(self, axis: int, with_vectors: bool = False):
+        n = self.n[axis]
+        lam = np.empty(n)
+        T = np.empty((n, n), order="F") if with_vectors else None
+        _check(lib().sem3d_get_eigs(self._h, axis, lam.ctypes.data_as(ctypes.c_void_p),
+                                    T.ctypes.data_as(ctypes.c_void_p) if T is not None else None), "sem3d_get_eigs")
+        return (lam, T) if with_vectors else lam
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().sem3d_destroy(self._h), "sem3d_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,141 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Inputs are seeded; the oracle sees the same arrays.  Tolerances (relative
+L-infinity against the oracle's refined FP64 solve):
+  * FP64 mode products + 1 FP64 refinement sweep : 1e-12
+  * FP64 mode products, no sweep                  : 1e-10 (bare solve, n*eps-level)
+  * BF16x3 mode products, no sweep                : 5e-4 (about 16-bit operands,
+    error amplified by the condition of the 1D bases; measured, not a target)
+  * BF16x3 + 3 FP64 sweeps                        : 1e-12
+The H-form operator apply is pure FP64 with a different summation order than
+the oracle's sparse products: 1e-13 relative to max |Au|.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import apply_h, refined_solve, sem_1d
+from paper_2310_00226_gb300.inputs import random_rhs, sine_123
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sem3d():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2310_00226_gb300 import sem3d as mod
+    mod.lib()  # raises if the native library is missing
+    return mod
+
+
+def _axes(n3, k, L3):
+    return [sem_1d(k, (n + 1) // k, 0.0, Lb) for n, Lb in zip(n3, L3)]
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+GRIDS = [
+    # (nx, ny, nz), k, (Lx, Ly, Lz), c
+    ((1, 1, 1), 1, (1.0, 1.0, 1.0), 0.0),
+    ((1, 3, 7), 2, (1.0, 0.5, 2.0), 1.0),
+    ((7, 11, 5), 2, (1.0, 1.3, 0.8), 0.0),
+    ((63, 39, 47), 2, (1.0, 1.0, 1.0), 3.0),
+    ((129, 65, 33), 2, (1.0, 0.5, 0.25), 0.5),
+    ((383, 63, 95), 4, (1.0, 1.0, 1.0), 1.0),
+    ((255, 191, 127), 4, (1.0, 1.0, 1.0), 10.0),
+]
+
+
+def _case(i):
+    n3, k, L3, c = GRIDS[i]
+    sx, sy, sz = _axes(n3, k, L3)
+    F = random_rhs(*n3, seed=100 + i)
+    return n3, k, L3, c, (sx, sy, sz), F
+
+
+@pytest.mark.parametrize("i", range(len(GRIDS)))
+def test_apply_matches_oracle(sem3d, i):
+    n3, k, L3, c, (sx, sy, sz), U = _case(i)
+    ref = apply_h(U, sx, sy, sz, c)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        u = torch.from_numpy(U).cuda()
+        Au = torch.empty_like(u)
+        p.apply(u, Au)
+        p.sync_check()
+        got = Au.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("i", range(len(GRIDS)))
+def test_fp64_solve_matches_oracle(sem3d, i):
+    n3, k, L3, c, (sx, sy, sz), F = _case(i)
+    ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.set_precision("fp64", 0)
+        p.solve(f, u)
+        p.sync_check()
+        bare = u.cpu().numpy()
+        p.set_precision("fp64", 1)
+        p.solve(f, u)
+        p.sync_check()
+        refined = u.cpu().numpy()
+    assert _rel(bare, ref) < 1e-10
+    assert _rel(refined, ref) < 1e-12
+
+
+@pytest.mark.parametrize("i", range(len(GRIDS)))
+def test_bf16x3_solve_matches_oracle(sem3d, i):
+    n3, k, L3, c, (sx, sy, sz), F = _case(i)
+    ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.set_precision("bf16x3", 0)
+        p.solve(f, u)
+        p.sync_check()
+        bare = u.cpu().numpy()
+        p.set_precision("bf16x3", 3)
+        p.solve(f, u)
+        p.sync_check()
+        refined = u.cpu().numpy()
+    assert _rel(bare, ref) < 5e-4
+    assert _rel(refined, ref) < 1e-12
+
+
+def test_q2_n63_manufactured_both_paths(sem3d):
+    # Q^2, Ne = 32 on [0,1]^3, n = 63, -Lap u = f, u = sin(pi x) sin(2 pi y) sin(3 pi z).
+    s = sem_1d(2, 32, 0.0, 1.0)
+    u_ex, F = sine_123(s.x, s.x, s.x)
+    ref = refined_solve(F, s, s, s, 0.0, sweeps=1)
+    with sem3d.Plan(63, 63, 63, 2, (1.0, 1.0, 1.0), 0.0) as p:
+        np.testing.assert_allclose(p.nodes(0), s.x, atol=1e-15)
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        for prec, sw in (("fp64", 1), ("bf16x3", 3)):
+            p.set_precision(prec, sw)
+            p.solve(f, u)
+            p.sync_check()
+            got = u.cpu().numpy()
+            assert _rel(got, ref) < 1e-12, prec
+            assert np.abs(got - u_ex).max() < 2e-5, prec
+
+
+def test_solve_is_repeatable_and_stream_ordered(sem3d):
+    n3, k, L3, c, (sx, sy, sz), F = _case(3)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        p.set_precision("bf16x3", 2)
+        s = torch.cuda.Stream()
+        f = torch.from_numpy(F).cuda()
+        u1 = torch.empty_like(f)
+        u2 = torch.empty_like(f)
+        with torch.cuda.stream(s):
+            p.solve(f, u1, stream=s)
+            p.solve(f, u2, stream=s)
+        p.sync_check(stream=s)
+        assert torch.equal(u1, u2)
