@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark of the Q^k spectral-element fast-diagonalisation solve on GB300.
+
+Workload (one "step" = one full solve of the hot path): Q^4 SEM, 250 elements
+per axis on [0,1]^3, n = 999 interior nodes per axis (997,002,999 DoF),
+-Lap u + u = f with f from the manufactured u = e^x sin(pi x) sin(pi y)
+sin(pi z), homogeneous Dirichlet data.  The headline path is the tcgen05
+split-bf16 (BF16x3) solve with 3 FP64 refinement sweeps (error ~1e-13 against
+FP64); the plain FP64 DMMA path (+1 FP64 sweep) is timed beside it.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", str(os.cpu_count() or 1))
+os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1000^3 Q^4 solve ms & GDoF/s on 1 GB300: FP64 vs refined split-BF16 at 1e-12 err"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return PEAKS_FALLBACK, "fallback"
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------- oracle baseline
+
+def oracle_sample(n: int, k: int, c: float, lines: int = 63):
+    """Time the FP64 oracle (test infrastructure, numpy + BLAS on the host
+    cores) on a bounded sample of the n^3 workload: each of its mode products
+    along x, y and z and its H-form apply, run on `lines`-thick slabs of the
+    full-length grid lines.  Every grid line costs the same, so the time of
+    the oracle's refined solve of the whole grid (2 fast solves of 6 mode
+    products each + 1 apply) is the sum scaled by n / lines."""
+    from oracle import sem_1d
+    from oracle.sem import apply_h, mode_product
+    s = sem_1d(k, (n + 1) // k, 0.0, 1.0)
+    s_lines = sem_1d(k, (lines + 1) // k, 0.0, 1.0)  # same k: same band cost per node
+    rng = np.random.Generator(np.random.PCG64(7))
+    slab_xy = rng.standard_normal((lines, n, n))          # (z, y, x): `lines` z-pages
+    slab_z = rng.standard_normal((n, lines, n))           # `lines` y-rows, full z
+    t = {}
+    t0 = time.perf_counter(); mode_product(slab_xy.T, s.Tinv, 0); t["x"] = time.perf_counter() - t0
+    t0 = time.perf_counter(); mode_product(slab_xy.T, s.Tinv, 1); t["y"] = time.perf_counter() - t0
+    t0 = time.perf_counter(); mode_product(slab_z.T, s.Tinv, 2); t["z"] = time.perf_counter() - t0
+    lam3 = s.lam[:, None, None] + s.lam[None, :, None] + s.lam[None, None, :lines] + c
+    t0 = time.perf_counter(); _ = slab_xy.T / lam3; t["div"] = time.perf_counter() - t0
+    t0 = time.perf_counter(); apply_h(slab_xy, s, s, s_lines, c); t["apply"] = time.perf_counter() - t0
+    scale = n / lines
+    solve = 2 * (t["x"] + t["y"] + t["z"]) + t["div"]
+    total = (2 * solve + t["apply"]) * scale
+    return total, sum(t.values())
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    n, k, c = args.n, 4, 1.0
+    dofs = n**3
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    lines = args.oracle_lines
+    for _ in range(args.warmup):
+        oracle_sample(n, k, c, lines)
+    est, spent = [], 0.0
+    for _ in range(args.steps):
+        e, sp = oracle_sample(n, k, c, lines)
+        est.append(e)
+        spent += sp
+    ms = float(np.mean(est)) * 1e3
+    value = dofs / (ms / 1e3) / 1e9
+    sample = (f"oracle (numpy/BLAS FP64) mode products along x, y, z and H-form apply on {lines}-line slabs "
+              f"of the n={n} grid; refined-solve time = (2 fast solves + 1 apply) x {n}/{lines}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"q4_n{n}_expsine", "n": n, "k": k, "c": c, "dofs": dofs},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_seconds_per_step": spent / max(1, args.steps)},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- our path
+
+def timed(fn, steps, warmup, stream, torch, dist=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    from paper_2310_00226_gb300 import sem3d
+    from paper_2310_00226_gb300.inputs import exp_sine
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = load_peaks()
+    n, k, c = args.n, 4, 1.0
+    dofs = n**3
+    t_setup = time.perf_counter()
+    plan = sem3d.Plan(n, n, n, k, (1.0, 1.0, 1.0), c)
+    t_setup = time.perf_counter() - t_setup
+    x = plan.nodes(0)
+    u_ex_h, f_h = exp_sine(x, x, x, c)
+    f = torch.from_numpy(f_h).cuda()
+    u = torch.empty_like(f)
+
+    # ---- headline: BF16x3 + FP64 refinement sweeps
+    plan.set_precision("bf16x3", args.sweeps)
+    step = lambda: plan.solve(f, u, stream)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    plan.sync_check(stream)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    plan.profile(True)
+    launches0 = plan.launch_count()
+    ms = timed(step, args.steps, 0, stream, torch, dist)
+    launches = plan.launch_count() - launches0
+    tc_n, tc_ms = plan.profile_read("tc_mode_product")
+    st_n, st_ms = plan.profile_read("stencil")
+    sp_n, sp_ms = plan.profile_read("split")
+    plan.profile(False)
+    clocks = clk.stop()
+    plan.sync_check(stream)
+    u_bf = u.clone()
+
+    # accuracy of the headline result
+    u_ex = torch.from_numpy(u_ex_h).cuda()
+    err_exact = float((u_bf - u_ex).abs().max() / u_ex.abs().max())
+    del u_ex
+    Au = torch.empty_like(f)
+    plan.apply(u_bf, Au, stream)
+    rel_res = float((f - Au).abs().max() / f.abs().max())
+    del Au
+
+    # ---- plain FP64 DMMA path (+1 FP64 sweep)
+    fp64 = None
+    if args.fp64_steps > 0:
+        plan.set_precision("fp64", 1)
+        plan.profile(True)
+        ms64 = timed(step, args.fp64_steps, args.fp64_warmup, stream, torch, dist)
+        f64_n, f64_ms = plan.profile_read("f64_mode_product")
+        plan.profile(False)
+        plan.sync_check(stream)
+        diff = float((u - u_bf).abs().max() / u.abs().max())
+        fp64 = {"ms_per_step": ms64, "value": dofs * world / (ms64 / 1e3) / 1e9, "unit": "GDoF/s",
+                "steps": args.fp64_steps, "warmup": args.fp64_warmup, "path": "FP64 DMMA mode products + 1 FP64 sweep",
+                "rel_linf_bf16x3_vs_fp64": diff, "speedup_bf16x3_over_fp64": ms64 / ms,
+                "dmma_kernel_avg_ms": f64_ms / max(1, f64_n),
+                "dmma_achieved_tflops": 2.0 * n**4 / (f64_ms / max(1, f64_n) / 1e3) / 1e12}
+        plan.set_precision("bf16x3", args.sweeps)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e:
+        f_pin = torch.from_numpy(f_h).pin_memory()
+        u_pin = torch.empty(f_h.shape, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            f.copy_(f_pin, non_blocking=True)
+            plan.solve(f, u, stream)
+            u_pin.copy_(u, non_blocking=True)
+
+        ms_e2e = timed(e2e_step, args.steps, args.warmup, stream, torch, dist)
+        e2e = {"value": dofs * world / (ms_e2e / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)}
+        del f_pin, u_pin
+
+    # ---- roofline of the dominant kernel (tcgen05 BF16x3 mode product)
+    tc_avg_ms = tc_ms / max(1, tc_n)
+    flops_per_launch = 3 * 2.0 * n**4  # 3 bf16 products per useful FMA, 2 flops each, n^4 FMA per pass
+    achieved = flops_per_launch / (tc_avg_ms / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
+    roofline = {"kernel": "mode_product_bf16x3 (tcgen05)", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": tc_avg_ms, "launches": tc_n,
+                "share_of_step": tc_ms / (ms * args.steps)}
+    kernels = {"tc_mode_product": {"launches": tc_n, "avg_ms": tc_avg_ms},
+               "stencil_residual": {"launches": st_n, "avg_ms": st_ms / max(1, st_n),
+                                    "fp64_tflops": 2 * 21.0 * dofs / (st_ms / max(1, st_n) / 1e3) / 1e12},
+               "split": {"launches": sp_n, "avg_ms": sp_ms / max(1, sp_n),
+                         "gbs": 12.0 * dofs / (sp_ms / max(1, sp_n) / 1e3) / 1e9}}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        est, spent = oracle_sample(n, k, c, args.oracle_lines)
+        cpu = {"value": dofs / est / 1e9, "unit": "GDoF/s", "ms_per_solve": est * 1e3,
+               "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": (f"oracle mode products along x, y, z and H-form apply on {args.oracle_lines}-line slabs "
+                          f"of the n={n} grid (refined solve = 2 fast solves + 1 apply, scaled by "
+                          f"{n}/{args.oracle_lines}); {spent:.1f} s of CPU work")}
+
+    line = {
+        "metric": METRIC, "value": dofs * world / (ms / 1e3) / 1e9, "unit": "GDoF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate) + f64 refinement", "data": "synthetic",
+        "config": {"workload": f"q4_n{n}_expsine: Q^4, Ne={(n + 1) // k}/axis on [0,1]^3, n={n}, {dofs} DoF, "
+                               "-Lap u + u = f, u = e^x sin(pi x) sin(pi y) sin(pi z), Dirichlet",
+                   "path": f"tcgen05 BF16x3 mode products + {args.sweeps} FP64 refinement sweeps",
+                   "l2": "inputs larger than L2 (8 GB FP64 per array, 4 GB split-bf16 per pass)",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": t_setup},
+        "accuracy": {"rel_linf_vs_exact_solution": err_exact, "rel_residual_linf": rel_res},
+        "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
+        "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=999, help="interior nodes per axis (n+1 divisible by 4)")
+    ap.add_argument("--sweeps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--oracle-lines", type=int, default=63, help="slab thickness; (lines+1) % 4 == 0")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

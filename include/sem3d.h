@@ -132,6 +132,20 @@ sem3d_status sem3d_axis_info(int n, int k, double L, double* x, double* M, doubl
  * recorded flags.  Synchronous with respect to the host. */
 sem3d_status sem3d_sync_check(sem3d_handle h, void* stream);
 
+/* Per-kernel timing for measurement tools.  sem3d_profile(h, 1) discards
+ * earlier records and, from then on, brackets every kernel launch of this plan
+ * with CUDA events recorded on the launch's stream; sem3d_profile(h, 0) stops.
+ * sem3d_profile_read synchronises on the recorded events and returns, for one
+ * kernel class, the number of kernels launched and their summed device time
+ * in milliseconds.  Kernel classes: 0 = tensor-core (tcgen05) mode product,
+ * 1 = FP64 (DMMA) mode product, 2 = FP64 stencil / residual, 3 = FP64 ->
+ * split-bf16 conversion. */
+sem3d_status sem3d_profile(sem3d_handle h, int enable);
+sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms);
+
+/* Total number of kernels this plan has launched since sem3d_setup. */
+sem3d_status sem3d_launch_count(sem3d_handle h, unsigned long long* count);
+
 /* Release the plan and every device buffer it allocated (not caller-owned
  * workspace).  Synchronises the device first.  NULL is accepted. */
 sem3d_status sem3d_destroy(sem3d_handle h);

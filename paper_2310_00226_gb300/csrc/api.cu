@@ -71,6 +71,14 @@ struct sem3d_plan {
   bool ws_owned = false;
   int* d_err = nullptr;
   std::vector<void*> owned;  // device allocations made at setup
+  // launch accounting and optional per-kernel timing
+  unsigned long long launches = 0;
+  bool profiling = false;
+  struct EvPair { int kind; int count; cudaEvent_t a, b; };
+  std::vector<EvPair> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[4] = {0, 0, 0, 0};
+  long long prof_n[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -102,6 +110,47 @@ void split_matrix(const std::vector<double>& W, int n, int Kp, std::vector<__nv_
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Kernel classes for sem3d_profile_read.
+enum { K_TC = 0, K_F64 = 1, K_STENCIL = 2, K_SPLIT = 3 };
+
+cudaEvent_t take_event(sem3d_plan* p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Bracket one launch site (`count` kernels) with events when profiling.
+struct LaunchScope {
+  sem3d_plan* p;
+  int kind, count;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  LaunchScope(sem3d_plan* p_, int kind_, int count_, cudaStream_t s_) : p(p_), kind(kind_), count(count_), s(s_) {
+    if (p->profiling && (a = take_event(p)) != nullptr) cudaEventRecord(a, s);
+  }
+  void done() {
+    p->launches += (unsigned long long)count;
+    if (!a) return;
+    cudaEvent_t b = take_event(p);
+    if (!b) { p->pool.push_back(a); return; }
+    cudaEventRecord(b, s);
+    p->pending.push_back({kind, count, a, b});
+  }
+};
+
+#define LAUNCH(plan, kind, count, stream, expr)           \
+  do {                                                    \
+    LaunchScope _ls((plan), (kind), (count), (stream));   \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);   \
+    _ls.done();                                           \
+  } while (0)
 
 // Workspace layout per mode.
 //   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
@@ -135,12 +184,12 @@ sem3d_status solve_once_f64(sem3d_plan* p, const double* in, double* out, bool a
   double* B = reinterpret_cast<double*>(static_cast<char*>(p->ws) + align256(N * sizeof(double)));
   const Geom& g = p->g;
   const DevAxis* d = p->dev;
-  CUDA_TRY(launch_mode_product_f64(g, 2, d[2].Tinv, in, A, EPI_STORE, nullptr, nullptr, nullptr, s));
-  CUDA_TRY(launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
-  CUDA_TRY(launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_DIV, d[0].lam, d[1].lam, d[2].lam, s));
-  CUDA_TRY(launch_mode_product_f64(g, 2, d[2].T, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
-  CUDA_TRY(launch_mode_product_f64(g, 1, d[1].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
-  CUDA_TRY(launch_mode_product_f64(g, 0, d[0].T, A, out, accumulate ? EPI_ACCUM : EPI_STORE, nullptr, nullptr,
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].Tinv, in, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_DIV, d[0].lam, d[1].lam, d[2].lam, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].T, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].T, A, out, accumulate ? EPI_ACCUM : EPI_STORE, nullptr, nullptr,
                                    nullptr, s));
   return SEM3D_OK;
 }
@@ -153,12 +202,12 @@ sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double
   const float *lx = d[0].lamf, *ly = d[1].lamf, *lz = d[2].lamf;
   const int sms = p->num_sms;
   int* e = p->d_err;
-  CUDA_TRY(launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  CUDA_TRY(launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  CUDA_TRY(launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
-  CUDA_TRY(launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  CUDA_TRY(launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  CUDA_TRY(launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, out, accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz,
+  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
+  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, out, accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz,
                                       e, sms, s));
   return SEM3D_OK;
 }
@@ -271,7 +320,7 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
     double* r = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(N * sizeof(double)));
     if ((st = solve_once_f64(h, f, u, false, s)) != SEM3D_OK) return st;
     for (int sw = 0; sw < h->sweeps; ++sw) {
-      CUDA_TRY(launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+      LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
       if ((st = solve_once_f64(h, r, u, true, s)) != SEM3D_OK) return st;
     }
   } else {
@@ -279,10 +328,11 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
     char* w = static_cast<char*>(h->ws);
     TcBuffers S0{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
     TcBuffers S1{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
-    CUDA_TRY(launch_split(h->g, f, S0.hi, S0.lo, s));
+    LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s));
     if ((st = solve_once_bf16x3(h, S0, S1, u, false, s)) != SEM3D_OK) return st;
     for (int sw = 0; sw < h->sweeps; ++sw) {
-      CUDA_TRY(launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
+      LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
+             launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
       if ((st = solve_once_bf16x3(h, S0, S1, u, true, s)) != SEM3D_OK) return st;
     }
   }
@@ -293,7 +343,8 @@ sem3d_status sem3d_apply(sem3d_handle h, const double* u, double* Au, void* stre
   if (!h || !u || !Au) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
   const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
   if (u < Au + N && Au < u + N) return fail(SEM3D_ERR_INVALID_ARG, "u and Au overlap");
-  CUDA_TRY(launch_stencil(h->g, h->k, h->dev, u, nullptr, Au, nullptr, nullptr, 0, static_cast<cudaStream_t>(stream)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, nullptr, Au, nullptr, nullptr, 0, s));
   return SEM3D_OK;
 }
 
@@ -346,9 +397,47 @@ sem3d_status sem3d_sync_check(sem3d_handle h, void* stream) {
   return SEM3D_OK;
 }
 
+sem3d_status sem3d_profile(sem3d_handle h, int enable) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  for (auto& ev : h->pending) {
+    cudaEventSynchronize(ev.b);
+    h->pool.push_back(ev.a);
+    h->pool.push_back(ev.b);
+  }
+  h->pending.clear();
+  for (int q = 0; q < 4; ++q) { h->prof_ms[q] = 0.0; h->prof_n[q] = 0; }
+  h->profiling = enable != 0;
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms) {
+  if (!h || kind < 0 || kind > 3) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
+  for (auto& ev : h->pending) {
+    CUDA_TRY(cudaEventSynchronize(ev.b));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    h->prof_ms[ev.kind] += ms;
+    h->prof_n[ev.kind] += ev.count;
+    h->pool.push_back(ev.a);
+    h->pool.push_back(ev.b);
+  }
+  h->pending.clear();
+  if (launches) *launches = h->prof_n[kind];
+  if (total_ms) *total_ms = h->prof_ms[kind];
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_launch_count(sem3d_handle h, unsigned long long* count) {
+  if (!h || !count) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  *count = h->launches;
+  return SEM3D_OK;
+}
+
 sem3d_status sem3d_destroy(sem3d_handle h) {
   if (!h) return SEM3D_OK;
   cudaError_t e = cudaDeviceSynchronize();
+  for (auto& ev : h->pending) { h->pool.push_back(ev.a); h->pool.push_back(ev.b); }
+  for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
   if (h->ws && h->ws_owned) cudaFree(h->ws);
   for (void* d : h->owned) cudaFree(d);
   delete h;

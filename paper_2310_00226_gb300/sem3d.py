@@ -34,6 +34,9 @@ EXPORTS = (
     "sem3d_get_eigs",
     "sem3d_axis_info",
     "sem3d_sync_check",
+    "sem3d_profile",
+    "sem3d_profile_read",
+    "sem3d_launch_count",
     "sem3d_destroy",
     "sem3d_last_error",
 )
@@ -67,6 +70,10 @@ def lib() -> ctypes.CDLL:
     L.sem3d_get_eigs.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
     L.sem3d_axis_info.argtypes = [c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_sync_check.argtypes = [c_void_p, c_void_p]
+    L.sem3d_profile.argtypes = [c_void_p, c_int]
+    L.sem3d_profile_read.argtypes = [c_void_p, c_int, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_double)]
+    L.sem3d_launch_count.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]
     L.sem3d_destroy.argtypes = [c_void_p]
     L.sem3d_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -148,6 +155,23 @@ class Plan:
 
     def sync_check(self, stream=None):
         _check(lib().sem3d_sync_check(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_sync_check")
+
+    KERNEL_CLASSES = {"tc_mode_product": 0, "f64_mode_product": 1, "stencil": 2, "split": 3}
+
+    def profile(self, enable: bool = True):
+        _check(lib().sem3d_profile(self._h, 1 if enable else 0), "sem3d_profile")
+
+    def profile_read(self, kind: str):
+        """(launches, total_ms) of one kernel class since profiling was enabled."""
+        n, ms = ctypes.c_longlong(), ctypes.c_double()
+        _check(lib().sem3d_profile_read(self._h, self.KERNEL_CLASSES[kind], ctypes.byref(n), ctypes.byref(ms)),
+               "sem3d_profile_read")
+        return n.value, ms.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_ulonglong()
+        _check(lib().sem3d_launch_count(self._h, ctypes.byref(n)), "sem3d_launch_count")
+        return n.value
 
     def nodes(self, axis: int) -> np.ndarray:
         x = np.empty(self.n[axis])
