@@ -213,6 +213,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ms = timed(step, args.steps, 0, stream, torch, dist)
     launches = plan.launch_count() - launches0
     tc_n, tc_ms = plan.profile_read("tc_mode_product")
+    per_pass = {}
+    for key in ("tc_x", "tc_y", "tc_z", "tc_f64_out"):
+        pn, pms = plan.profile_read(key)
+        per_pass[key] = {"launches": pn, "avg_ms": pms / max(1, pn)}
     st_n, st_ms = plan.profile_read("stencil")
     sp_n, sp_ms = plan.profile_read("split")
     plan.profile(False)
@@ -272,7 +276,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": tc_avg_ms, "launches": tc_n,
                 "share_of_step": tc_ms / (ms * args.steps)}
-    kernels = {"tc_mode_product": {"launches": tc_n, "avg_ms": tc_avg_ms},
+    kernels = {"tc_mode_product": {"launches": tc_n, "avg_ms": tc_avg_ms, "per_pass": per_pass},
                "stencil_residual": {"launches": st_n, "avg_ms": st_ms / max(1, st_n),
                                     "fp64_tflops": 2 * 21.0 * dofs / (st_ms / max(1, st_n) / 1e3) / 1e12},
                "split": {"launches": sp_n, "avg_ms": sp_ms / max(1, sp_n),

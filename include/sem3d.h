@@ -139,7 +139,9 @@ sem3d_status sem3d_sync_check(sem3d_handle h, void* stream);
  * kernel class, the number of kernels launched and their summed device time
  * in milliseconds.  Kernel classes: 0 = tensor-core (tcgen05) mode product,
  * 1 = FP64 (DMMA) mode product, 2 = FP64 stencil / residual, 3 = FP64 ->
- * split-bf16 conversion. */
+ * split-bf16 conversion; the tensor-core launches of class 0 are also counted
+ * by pass: 4 = x pass, 5 = y pass, 6 = z pass writing split-bf16 output,
+ * 7 = the last pass of a solve (writes or accumulates FP64 u). */
 sem3d_status sem3d_profile(sem3d_handle h, int enable);
 sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms);
 

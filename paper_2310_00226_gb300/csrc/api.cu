@@ -74,11 +74,11 @@ struct sem3d_plan {
   // launch accounting and optional per-kernel timing
   unsigned long long launches = 0;
   bool profiling = false;
-  struct EvPair { int kind; int count; cudaEvent_t a, b; };
+  struct EvPair { int kind, sub, count; cudaEvent_t a, b; };
   std::vector<EvPair> pending;
   std::vector<cudaEvent_t> pool;
-  double prof_ms[4] = {0, 0, 0, 0};
-  long long prof_n[4] = {0, 0, 0, 0};
+  double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -111,8 +111,9 @@ void split_matrix(const std::vector<double>& W, int n, int Kp, std::vector<__nv_
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Kernel classes for sem3d_profile_read.
-enum { K_TC = 0, K_F64 = 1, K_STENCIL = 2, K_SPLIT = 3 };
+// Kernel classes for sem3d_profile_read; tensor-core launches are also
+// counted per pass (x / y / z, and the last pass that writes FP64 u).
+enum { K_TC = 0, K_F64 = 1, K_STENCIL = 2, K_SPLIT = 3, K_TC_X = 4, K_TC_Y = 5, K_TC_Z = 6, K_TC_F64OUT = 7 };
 
 cudaEvent_t take_event(sem3d_plan* p) {
   if (!p->pool.empty()) {
@@ -128,10 +129,11 @@ cudaEvent_t take_event(sem3d_plan* p) {
 // Bracket one launch site (`count` kernels) with events when profiling.
 struct LaunchScope {
   sem3d_plan* p;
-  int kind, count;
+  int kind, sub, count;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
-  LaunchScope(sem3d_plan* p_, int kind_, int count_, cudaStream_t s_) : p(p_), kind(kind_), count(count_), s(s_) {
+  LaunchScope(sem3d_plan* p_, int kind_, int sub_, int count_, cudaStream_t s_)
+      : p(p_), kind(kind_), sub(sub_), count(count_), s(s_) {
     if (p->profiling && (a = take_event(p)) != nullptr) cudaEventRecord(a, s);
   }
   void done() {
@@ -140,17 +142,18 @@ struct LaunchScope {
     cudaEvent_t b = take_event(p);
     if (!b) { p->pool.push_back(a); return; }
     cudaEventRecord(b, s);
-    p->pending.push_back({kind, count, a, b});
+    p->pending.push_back({kind, sub, count, a, b});
   }
 };
 
-#define LAUNCH(plan, kind, count, stream, expr)           \
+#define LAUNCH_SUB(plan, kind, sub, count, stream, expr)  \
   do {                                                    \
-    LaunchScope _ls((plan), (kind), (count), (stream));   \
+    LaunchScope _ls((plan), (kind), (sub), (count), (stream)); \
     cudaError_t _e = (expr);                              \
     if (_e != cudaSuccess) return cuda_fail(_e, #expr);   \
     _ls.done();                                           \
   } while (0)
+#define LAUNCH(plan, kind, count, stream, expr) LAUNCH_SUB(plan, kind, -1, count, stream, expr)
 
 // Workspace layout per mode.
 //   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
@@ -202,12 +205,16 @@ sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double
   const float *lx = d[0].lamf, *ly = d[1].lamf, *lz = d[2].lamf;
   const int sms = p->num_sms;
   int* e = p->d_err;
-  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
-  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH(p, K_TC, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, out, accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz,
+  // Forward: z, y, x with the division fused into the x pass (Eq. 13).
+  LAUNCH_SUB(p, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
+  // Backward: x, y, z.  The mode products commute, so the order is free; the
+  // z pass goes last because its TMEM lanes run along the contiguous index,
+  // which makes the FP64 read-modify-write of u coalesced.
+  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_F64OUT, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out, accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz,
                                       e, sms, s));
   return SEM3D_OK;
 }
@@ -405,19 +412,23 @@ sem3d_status sem3d_profile(sem3d_handle h, int enable) {
     h->pool.push_back(ev.b);
   }
   h->pending.clear();
-  for (int q = 0; q < 4; ++q) { h->prof_ms[q] = 0.0; h->prof_n[q] = 0; }
+  for (int q = 0; q < 8; ++q) { h->prof_ms[q] = 0.0; h->prof_n[q] = 0; }
   h->profiling = enable != 0;
   return SEM3D_OK;
 }
 
 sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms) {
-  if (!h || kind < 0 || kind > 3) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
+  if (!h || kind < 0 || kind > 7) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
   for (auto& ev : h->pending) {
     CUDA_TRY(cudaEventSynchronize(ev.b));
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
     h->prof_ms[ev.kind] += ms;
     h->prof_n[ev.kind] += ev.count;
+    if (ev.sub >= 0) {
+      h->prof_ms[ev.sub] += ms;
+      h->prof_n[ev.sub] += ev.count;
+    }
     h->pool.push_back(ev.a);
     h->pool.push_back(ev.b);
   }

@@ -21,8 +21,9 @@
 // 128 rows x 256 outputs):
 //   warp 0      : TMA producer (one thread)
 //   warp 1      : TMEM allocator + MMA issuer (one thread)
-//   warps 2..5  : epilogue (TMEM -> registers -> global), 128 threads
-// Shared memory holds STAGES stages of {A_hi, A_lo, W_hi, W_lo} K-slices of 64;
+//   warps 2..9  : epilogue (TMEM -> registers -> global), two warps per TMEM
+//                 lane quadrant, each on half of the tile's columns
+// Shared memory holds STAGES = 4 stages of {A_hi, A_lo, W_hi, W_lo} K-slices of 32;
 // TMEM holds two 128 x 256 FP32 accumulators so the epilogue of one tile
 // overlaps the MMAs of the next.  Every wait is bounded: on expiry the kernel
 // records SEM3D_ERR_TIMEOUT in *err, drains its own copies and MMAs, frees
@@ -39,14 +40,15 @@ namespace {
 
 constexpr int BM = 128;           // tile rows = TMEM lanes
 constexpr int BN = 256;           // tile outputs = TMEM columns per accumulator
-constexpr int BK = 64;            // K per stage: one 128-byte swizzle row of bf16
-constexpr int STAGES = 2;
-constexpr int A_TILE_BYTES = BM * BK * 2;  // 16 KB
-constexpr int B_TILE_BYTES = BN * BK * 2;  // 32 KB
+constexpr int BK = 32;            // K per stage: one 64-byte swizzle row of bf16 (K-major tiles)
+constexpr int STAGES = 4;
+constexpr int A_TILE_BYTES = BM * BK * 2;  // 8 KB
+constexpr int B_TILE_BYTES = BN * BK * 2;  // 16 KB
 constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 2 * BN;  // 512
-constexpr int NUM_THREADS = 192;
+constexpr int EPI_WARPS = 8;                       // two per TMEM lane quadrant
+constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA, epilogue
 constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s per wait
 
 // ---------------------------------------------------------------- PTX helpers
@@ -121,15 +123,16 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (>>4), fixed version 1 at bit 46, 128-byte swizzle
-// (layout code 2 at bits 61-63).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// stride byte offsets (>>4), fixed version 1 at bit 46, swizzle layout code
+// at bits 61-63 (2 = 128-byte swizzle, 4 = 64-byte swizzle).
+constexpr uint32_t LAYOUT_SW128 = 2, LAYOUT_SW64 = 4;
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)layout << 61;
   return d;
 }
 
@@ -172,9 +175,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // ---------------------------------------------------------------- kernel
 
 struct TcArgs {
-  int pass;            // 0 = x, 1 = y, 2 = z
-  int epi;             // EPI_STORE / EPI_DIV / EPI_ACCUM
-  int out_f64;         // 1: write FP64 dense n-pitch output
   int m_tiles, n_tiles, batches, k_blocks;
   int rows;            // valid tile rows per batch (x: ny*nz, y: Px, z: Px*ny)
   int nout;            // valid outputs (length of the output axis)
@@ -187,107 +187,123 @@ struct TcArgs {
   int* err;
 };
 
-// Split an FP32 value into bf16 hi + lo.
-__device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
-  h = __float2bfloat16_rn(v);
-  l = __float2bfloat16_rn(v - __bfloat162float(h));
+// Output modes of the epilogue.
+enum : int { OUT_SPLIT = 0, OUT_DIV_SPLIT = 1, OUT_F64 = 2, OUT_F64_ACCUM = 3 };
+
+// Split two FP32 values into bf16 hi + lo pairs (packed bf16x2: element 0 in
+// the low half).  hi = rn(v), lo = rn(v - hi).
+__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(v1), "f"(v0));
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(v1 - h1), "f"(v0 - h0));
 }
 
+__device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
+  asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"((unsigned short)(v & 0xFFFFu)) : "memory");
+}
+
+// Epilogue of one 32-column chunk held by this thread: TMEM lane = `row`,
+// registers v[0..31] = columns col0 .. col0+31 of the output axis.
+//
+// x pass (PASS 0): row = (j,l) line, the output axis is contiguous in memory,
+//   so each thread writes 16-byte vectors of its own line.
+// y / z passes: row = contiguous index (i, or i + Px*j), the output axis has
+//   a stride, and the 32 lanes of a warp write 32 consecutive elements.
+template <int PASS, int MODE>
 __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32]) {
-  if (a.pass == 0) {
-    // row = (j,l) line, columns = output i (contiguous in memory).
+  const bool full = col0 + 32 <= a.nout;
+  if (PASS == 0) {
     if (row >= a.rows) return;
-    if (a.epi == EPI_DIV) {
+    if (MODE == OUT_DIV_SPLIT) {
       const int j = row % a.ny, l = row / a.ny;
-      const float s = a.lamy[j] + a.lamz[l] + a.c;
+      const float s = __ldg(a.lamy + j) + __ldg(a.lamz + l) + a.c;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int o = col0 + q;
-        const float d = (o < a.nout) ? __ldg(a.lamx + o) + s : 1.0f;
-        v[q] = v[q] / d;
+        const float d = (full || o < a.nout) ? __ldg(a.lamx + o) + s : 1.0f;
+        v[q] = __fdividef(v[q], d);
       }
     }
-    if (a.out_f64) {
-      double* dst = a.out64 + (long long)row * a.nx;
+    if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
+      double* dst = a.out64 + (size_t)row * a.nx + col0;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const int o = col0 + q;
-        if (o < a.nout) {
-          if (a.epi == EPI_ACCUM) dst[o] += (double)v[q];
-          else dst[o] = (double)v[q];
+        if (full || col0 + q < a.nout) {
+          if (MODE == OUT_F64_ACCUM) dst[q] += (double)v[q];
+          else dst[q] = (double)v[q];
         }
       }
     } else {
-      __nv_bfloat16* dh = a.out_hi + (long long)row * a.Px;
-      __nv_bfloat16* dl = a.out_lo + (long long)row * a.Px;
+      __nv_bfloat16* dh = a.out_hi + (size_t)row * a.Px + col0;
+      __nv_bfloat16* dl = a.out_lo + (size_t)row * a.Px + col0;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        const int o = col0 + 8 * g;
-        if (o + 8 > a.Px) break;  // Px is a multiple of 8
-        __align__(16) __nv_bfloat16 hh[8], ll[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) split2(v[8 * g + q], hh[q], ll[q]);
-        *reinterpret_cast<uint4*>(dh + o) = *reinterpret_cast<const uint4*>(hh);
-        *reinterpret_cast<uint4*>(dl + o) = *reinterpret_cast<const uint4*>(ll);
+        if (col0 + 8 * g + 8 > a.Px) break;  // Px is a multiple of 8
+        uint4 hh, ll;
+        split_pair(v[8 * g + 0], v[8 * g + 1], hh.x, ll.x);
+        split_pair(v[8 * g + 2], v[8 * g + 3], hh.y, ll.y);
+        split_pair(v[8 * g + 4], v[8 * g + 5], hh.z, ll.z);
+        split_pair(v[8 * g + 6], v[8 * g + 7], hh.w, ll.w);
+        *reinterpret_cast<uint4*>(dh + 8 * g) = hh;
+        *reinterpret_cast<uint4*>(dl + 8 * g) = ll;
       }
     }
     return;
   }
-  // y and z passes: row = contiguous index, columns = output mode (stride).
   if (row >= a.rows) return;
-  int i, j, l_fixed = 0;
-  long long rowoff, colstride;
-  if (a.pass == 1) {  // row = i, column = j (= b), batch = l
-    i = row; j = 0; l_fixed = batch;
-    rowoff = (long long)row + (long long)a.Px * a.ny * batch;
-    colstride = a.Px;
-  } else {            // row = i + Px*j, column = l
-    i = row % a.Px; j = row / a.Px;
-    rowoff = row;
-    colstride = (long long)a.Px * a.ny;
+  int i, j = 0;
+  uint32_t rowoff, cs;
+  if (PASS == 1) {  // row = i, column = j, batch = l
+    i = row;
+    rowoff = (uint32_t)row + (uint32_t)a.Px * (uint32_t)a.ny * (uint32_t)batch;
+    cs = (uint32_t)a.Px;
+  } else {          // row = i + Px*j, column = l
+    i = row % a.Px;
+    j = row / a.Px;
+    rowoff = (uint32_t)row;
+    cs = (uint32_t)a.Px * (uint32_t)a.ny;
   }
-  if (a.epi == EPI_DIV) {
-    const float li = __ldg(a.lamx + (i < a.nx ? i : 0));
+  if (MODE == OUT_DIV_SPLIT) {
+    const float li = __ldg(a.lamx + (i < a.nx ? i : 0)) + a.c;
+    const float fixed = (PASS == 1) ? __ldg(a.lamz + batch) : __ldg(a.lamy + j);
+    const float* lv = (PASS == 1) ? a.lamy : a.lamz;
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       const int o = col0 + q;
-      float d = 1.0f;
-      if (o < a.nout) {
-        if (a.pass == 1) d = li + __ldg(a.lamy + o) + __ldg(a.lamz + l_fixed) + a.c;
-        else d = li + __ldg(a.lamy + j) + __ldg(a.lamz + o) + a.c;
-      }
-      v[q] = v[q] / d;
+      const float d = (full || o < a.nout) ? li + fixed + __ldg(lv + o) : 1.0f;
+      v[q] = __fdividef(v[q], d);
     }
   }
-  if (a.out_f64) {
+  if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
     if (i >= a.nx) return;
-    long long base, cs;
-    if (a.pass == 1) { base = (long long)i + (long long)a.nx * a.ny * batch; cs = a.nx; }
-    else { base = (long long)i + (long long)a.nx * j; cs = (long long)a.nx * a.ny; }
+    size_t base, cs64;
+    if (PASS == 1) { base = (size_t)i + (size_t)a.nx * a.ny * batch; cs64 = (size_t)a.nx; }
+    else { base = (size_t)i + (size_t)a.nx * j; cs64 = (size_t)a.nx * a.ny; }
+    double* p = a.out64 + base + (size_t)col0 * cs64;
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
-      const int o = col0 + q;
-      if (o < a.nout) {
-        double* p = a.out64 + base + (long long)o * cs;
-        if (a.epi == EPI_ACCUM) *p += (double)v[q];
+      if (full || col0 + q < a.nout) {
+        if (MODE == OUT_F64_ACCUM) *p += (double)v[q];
         else *p = (double)v[q];
       }
+      p += cs64;
     }
   } else {
+    __nv_bfloat16* ph = a.out_hi + rowoff + (size_t)col0 * cs;
+    __nv_bfloat16* pl = a.out_lo + rowoff + (size_t)col0 * cs;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int o = col0 + q;
-      if (o < a.nout) {
-        __nv_bfloat16 h, l;
-        split2(v[q], h, l);
-        const long long off = rowoff + (long long)o * colstride;
-        a.out_hi[off] = h;
-        a.out_lo[off] = l;
-      }
+    for (int q = 0; q < 32; q += 2) {
+      uint32_t hh, ll;
+      split_pair(v[q], v[q + 1], hh, ll);
+      if (full || col0 + q < a.nout) { st_b16(ph, hh); st_b16(pl, ll); }
+      ph += cs; pl += cs;
+      if (full || col0 + q + 1 < a.nout) { st_b16(ph, hh >> 16); st_b16(pl, ll >> 16); }
+      ph += cs; pl += cs;
     }
   }
 }
 
+template <int PASS, int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -305,11 +321,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool a_mn = (a.pass != 0);
+  constexpr bool a_mn = (PASS != 0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), EPI_WARPS); }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -345,10 +361,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
         mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
         const int k0 = kb * BK;
-        if (a.pass == 0) {
+        if (PASS == 0) {
           tma_load_2d(a_hi, &tmA_hi, full_bar(s), k0, m0);
           tma_load_2d(a_lo, &tmA_lo, full_bar(s), k0, m0);
-        } else if (a.pass == 1) {
+        } else if (PASS == 1) {
           tma_load_3d(a_hi, &tmA_hi, full_bar(s), m0, k0, b);
           tma_load_3d(a_hi + A_TILE_BYTES / 2, &tmA_hi, full_bar(s), m0 + 64, k0, b);
           tma_load_3d(a_lo, &tmA_lo, full_bar(s), m0, k0, b);
@@ -369,13 +385,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_wait(full_bar(q % STAGES), (q / STAGES) & 1, nullptr);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer
-    constexpr uint32_t idesc_k = make_idesc(BM, BN, false);
-    constexpr uint32_t idesc_mn = make_idesc(BM, BN, true);
-    const uint32_t idesc = a_mn ? idesc_mn : idesc_k;
-    // A: K-major -> SBO 1024 (8-row groups), advance 32 B per K=16.
-    //    MN-major -> LBO 8192 (next 64-row block), SBO 1024 (next 8 K rows),
-    //    advance 2048 B per K=16.
-    const uint32_t a_lbo = a_mn ? 8192u : 16u, a_sbo = 1024u, a_kstep = a_mn ? 2048u : 32u;
+    constexpr uint32_t idesc = make_idesc(BM, BN, a_mn);
+    // K-major tiles (rows of BK = 32 bf16 = 64 B, 64-byte swizzle): SBO 512
+    //   (next 8-row group), advance 32 B per K = 16 inside the swizzled row.
+    // MN-major A (64 rows = 128 B per K row, 128-byte swizzle): LBO 4096 (next
+    //   64-row half of the tile), SBO 1024 (next 8 K rows), advance 2048 B per
+    //   K = 16.
+    constexpr uint32_t a_lbo = a_mn ? 4096u : 16u, a_sbo = a_mn ? 1024u : 512u, a_kstep = a_mn ? 2048u : 32u;
+    constexpr uint32_t a_layout = a_mn ? LAYOUT_SW128 : LAYOUT_SW64;
     int it = 0, tl = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++tl) {
@@ -392,10 +409,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
 #pragma unroll
         for (int k16 = 0; k16 < BK / 16; ++k16) {
-          const uint64_t dah = smem_desc(a_hi + k16 * a_kstep, a_lbo, a_sbo);
-          const uint64_t dal = smem_desc(a_lo + k16 * a_kstep, a_lbo, a_sbo);
-          const uint64_t dbh = smem_desc(b_hi + k16 * 32u, 16u, 1024u);
-          const uint64_t dbl = smem_desc(b_lo + k16 * 32u, 16u, 1024u);
+          const uint64_t dah = smem_desc(a_hi + k16 * a_kstep, a_lbo, a_sbo, a_layout);
+          const uint64_t dal = smem_desc(a_lo + k16 * a_kstep, a_lbo, a_sbo, a_layout);
+          const uint64_t dbh = smem_desc(b_hi + k16 * 32u, 16u, 512u, LAYOUT_SW64);
+          const uint64_t dbl = smem_desc(b_lo + k16 * 32u, 16u, 512u, LAYOUT_SW64);
           const uint32_t acc = (kb | k16) ? 1u : 0u;
           mma_bf16(tmem_d, dah, dbh, idesc, acc);
           mma_bf16(tmem_d, dah, dbl, idesc, 1u);
@@ -410,8 +427,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     mma_commit(drain_bar);
     mbar_wait(drain_bar, 0, nullptr);
   } else if (warp >= 2) {
-    // ------------------------------------------------ epilogue
-    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    // ------------------------------------------------ epilogue (EPI_WARPS warps)
+    // Warp w reads TMEM lane quadrant w % 4 (hardware rule) and one of
+    // EPI_WARPS/4 column slices of the tile.
+    const int quad = warp & 3;
+    const int slice = (warp - 2) >> 2;
+    constexpr int COLS = BN / (EPI_WARPS / 4);
     int tl = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++tl) {
       const int buf = tl & 1;
@@ -421,14 +442,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int rem = t - b * tiles_per_batch;
       const int mt = rem / a.n_tiles, nt = rem - mt * a.n_tiles;
       const int row = mt * BM + quad * 32 + lane;
-      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN);
+      const uint32_t taddr =
+          tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + slice * COLS);
 #pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        const int col0 = nt * BN + ch * 32;
+      for (int ch = 0; ch < COLS / 32; ++ch) {
+        const int col0 = nt * BN + slice * COLS + ch * 32;
         if (col0 >= a.nout) break;  // warp-uniform
         float v[32];
         tmem_ld32(taddr + ch * 32, v);
-        epilogue_chunk(a, row, col0, b, v);
+        epilogue_chunk<PASS, MODE>(a, row, col0, b, v);
       }
       tc_fence_before();
       __syncwarp();
@@ -461,7 +483,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
-              const uint32_t* box) {
+              const uint32_t* box, CUtensorMapSwizzle swz) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t gd[3], gs[2];
@@ -469,27 +491,55 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, 
   for (int r = 0; r < rank; ++r) { gd[r] = dims[r]; bx[r] = box[r]; }
   for (int r = 0; r + 1 < rank; ++r) gs[r] = strides_bytes[r];
   CUresult res = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return res == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
-                                       TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
-                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s) {
-  static bool attr_set = false;
+namespace {
+
+template <int PASS, int MODE>
+cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+                      const TcArgs& a, int grid, cudaStream_t s) {
+  static bool attr_set = false;  // per instantiation
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mode_product_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(mode_product_bf16x3_kernel<PASS, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  mode_product_bf16x3_kernel<PASS, MODE><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(a0, a1, b0, b1, a);
+  return cudaGetLastError();
+}
+
+template <int PASS>
+cudaError_t launch_tc_mode(int mode, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
+                           const CUtensorMap& b1, const TcArgs& a, int grid, cudaStream_t s) {
+  switch (mode) {
+    case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT>(a0, a1, b0, b1, a, grid, s);
+    case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT>(a0, a1, b0, b1, a, grid, s);
+    case OUT_F64: return launch_tc<PASS, OUT_F64>(a0, a1, b0, b1, a, grid, s);
+    default: return launch_tc<PASS, OUT_F64_ACCUM>(a0, a1, b0, b1, a, grid, s);
+  }
+}
+
+}  // namespace
+
+// K-major tiles are BK = 32 bf16 = 64 B wide (64-byte swizzle); MN-major
+// tiles are 64 elements = 128 B wide (128-byte swizzle).
+static constexpr CUtensorMapSwizzle SWZ_K = CU_TENSOR_MAP_SWIZZLE_64B;
+static constexpr CUtensorMapSwizzle SWZ_MN = CU_TENSOR_MAP_SWIZZLE_128B;
+
+cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
+                                       TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
+                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s) {
+  int mode;
+  if (out64) mode = (epi == EPI_ACCUM) ? OUT_F64_ACCUM : OUT_F64;
+  else mode = (epi == EPI_DIV) ? OUT_DIV_SPLIT : OUT_SPLIT;
+  if (out64 && epi == EPI_DIV) return cudaErrorInvalidValue;
   TcArgs a{};
-  a.pass = axis;
-  a.epi = epi;
-  a.out_f64 = out64 != nullptr;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
   a.out_hi = out.hi; a.out_lo = out.lo; a.out64 = out64;
   a.lamx = lamx; a.lamy = lamy; a.lamz = lamz; a.c = (float)g.c;
@@ -499,33 +549,34 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   bool ok = true;
   int nin = 0;
   if (axis == 0) {
-    // A: dims {i: nx, line: ny*nz}, line stride Px*2 B; box {64 (K), 128 rows}
+    // A: dims {i: nx, line: ny*nz}, line stride Px*2 B; box {BK (K), 128 rows}
     const uint64_t dims[2] = {(uint64_t)g.nx, ny * nz};
     const uint64_t str[1] = {Px * 2};
-    const uint32_t box[2] = {64, 128};
-    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box) && make_map(&mAl, in.lo, 2, dims, str, box);
+    const uint32_t box[2] = {BK, 128};
+    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box, SWZ_K) && make_map(&mAl, in.lo, 2, dims, str, box, SWZ_K);
     a.rows = g.ny * g.nz; a.batches = 1; nin = g.nx;
   } else if (axis == 1) {
-    // A: dims {i: Px, j: ny, l: nz}; box {64 rows, 64 K, 1}
+    // A: dims {i: Px, j: ny, l: nz}; box {64 rows, BK K, 1}
     const uint64_t dims[3] = {Px, ny, nz};
     const uint64_t str[2] = {Px * 2, Px * ny * 2};
-    const uint32_t box[3] = {64, 64, 1};
-    ok = ok && make_map(&mAh, in.hi, 3, dims, str, box) && make_map(&mAl, in.lo, 3, dims, str, box);
+    const uint32_t box[3] = {64, BK, 1};
+    ok = ok && make_map(&mAh, in.hi, 3, dims, str, box, SWZ_MN) && make_map(&mAl, in.lo, 3, dims, str, box, SWZ_MN);
     a.rows = g.Px; a.batches = g.nz; nin = g.ny;
   } else {
-    // A: dims {m = i + Px*j: Px*ny, l: nz}; box {64 rows, 64 K}
+    // A: dims {m = i + Px*j: Px*ny, l: nz}; box {64 rows, BK K}
     const uint64_t dims[2] = {Px * ny, nz};
     const uint64_t str[1] = {Px * ny * 2};
-    const uint32_t box[2] = {64, 64};
-    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box) && make_map(&mAl, in.lo, 2, dims, str, box);
+    const uint32_t box[2] = {64, BK};
+    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box, SWZ_MN) && make_map(&mAl, in.lo, 2, dims, str, box, SWZ_MN);
     a.rows = g.Px * g.ny; a.batches = 1; nin = g.nz;
   }
   {
-    // W: dims {t: n, o: n}, row pitch Kp*2 B; box {64 (K), 256 rows}
+    // W: dims {t: n, o: n}, row pitch Kp*2 B; box {BK (K), 256 rows}
     const uint64_t dims[2] = {(uint64_t)W.n, (uint64_t)W.n};
     const uint64_t str[1] = {(uint64_t)W.Kp * 2};
-    const uint32_t box[2] = {64, (uint32_t)BN};
-    ok = ok && make_map(&mBh, W.W_hi[which], 2, dims, str, box) && make_map(&mBl, W.W_lo[which], 2, dims, str, box);
+    const uint32_t box[2] = {BK, (uint32_t)BN};
+    ok = ok && make_map(&mBh, W.W_hi[which], 2, dims, str, box, SWZ_K) &&
+         make_map(&mBl, W.W_lo[which], 2, dims, str, box, SWZ_K);
   }
   if (!ok) return cudaErrorInvalidValue;
   a.nout = W.n;
@@ -535,8 +586,9 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   const long long total = (long long)a.m_tiles * a.n_tiles * a.batches;
   if (total >= (1LL << 31)) return cudaErrorInvalidValue;
   const int grid = (int)(total < num_sms ? total : num_sms);
-  mode_product_bf16x3_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
-  return cudaGetLastError();
+  if (axis == 0) return launch_tc_mode<0>(mode, mAh, mAl, mBh, mBl, a, grid, s);
+  if (axis == 1) return launch_tc_mode<1>(mode, mAh, mAl, mBh, mBl, a, grid, s);
+  return launch_tc_mode<2>(mode, mAh, mAl, mBh, mBl, a, grid, s);
 }
 
 }  // namespace sem3d

@@ -156,7 +156,8 @@ class Plan:
     def sync_check(self, stream=None):
         _check(lib().sem3d_sync_check(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_sync_check")
 
-    KERNEL_CLASSES = {"tc_mode_product": 0, "f64_mode_product": 1, "stencil": 2, "split": 3}
+    KERNEL_CLASSES = {"tc_mode_product": 0, "f64_mode_product": 1, "stencil": 2, "split": 3,
+                      "tc_x": 4, "tc_y": 5, "tc_z": 6, "tc_f64_out": 7}
 
     def profile(self, enable: bool = True):
         _check(lib().sem3d_profile(self._h, 1 if enable else 0), "sem3d_profile")
