@@ -152,6 +152,28 @@ sem3d_status sem3d_launch_count(sem3d_handle h, unsigned long long* count);
  * workspace).  Synchronises the device first.  NULL is accepted. */
 sem3d_status sem3d_destroy(sem3d_handle h);
 
+/* FP64 solve that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library call cudaMalloc,
+ * for example a program whose device memory belongs to another allocator, one
+ * that reserves all device memory up front, or one that must avoid the
+ * implicit device synchronisation cudaMalloc and cudaFree may cause.
+ *   Computes the same result as sem3d_solve in SEM3D_FP64 mode (DMMA mode
+ *   products and the plan's number of FP64 refinement sweeps, whatever
+ *   precision the plan is set to), with its scratch in one fixed device array
+ *   of 3 * 524288 doubles (12 MiB) compiled into the library: every GPU that
+ *   loads the library holds that array until the process exits.
+ *   Limit: nx*ny*nz <= 524288 (e.g. 63^3 or 80^3); larger grids return
+ *   SEM3D_ERR_INVALID_ARG with a message naming the limit.
+ *   f, u : device FP64 arrays as in sem3d_solve; must not overlap.
+ *   The current device must be the plan's device.  The first call on a device
+ *   looks up the array's device address (cudaGetSymbolAddress), so make that
+ *   first call before any stream capture.  No cudaMalloc, cudaFree or
+ *   allocating library call is made.
+ *   All calls share the one array and leave their intermediates in it; calls
+ *   whose work overlaps on the GPU (other streams, other threads, other plans
+ *   on the same device) race on it and must be serialised by the caller. */
+sem3d_status sem3d_solve_fp64_static(sem3d_handle h, const double* f, double* u, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* sem3d_last_error(void);
 

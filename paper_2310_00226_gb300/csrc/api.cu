@@ -457,3 +457,83 @@ sem3d_status sem3d_destroy(sem3d_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without any allocation.
+//
+// Some callers cannot let the library call cudaMalloc on their behalf: a
+// program whose device memory is owned by another allocator (a framework's
+// caching allocator that must account for every byte), one that reserves all
+// device memory when it starts, or one that must not pay the implicit device
+// synchronisation that cudaMalloc and cudaFree may perform in the middle of
+// its work.  sem3d_solve_fp64_static serves them: its scratch (the two
+// ping-pong arrays of the mode products and the residual array) is a fixed
+// file-scope device array that every GPU loading this library holds until the
+// process exits.  The caller still passes f and u.
+namespace {
+
+constexpr size_t kStaticMaxDofs = 524288;  // nx*ny*nz limit: 3 * 8 B * 524288 = 12 MiB
+static __device__ __align__(256) double g_static_scratch[3 * kStaticMaxDofs];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+double* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on device `dev` (which must be the
+// current device).  In host code the array's name is only a host-side
+// stand-in, so the address is asked from the runtime once per device.
+sem3d_status static_scratch(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(SEM3D_ERR_UNSUPPORTED, "device ordinal too large");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return SEM3D_OK;
+}
+
+sem3d_status solve_once_f64_into(sem3d_plan* p, const double* in, double* out, bool accumulate, double* A, double* B,
+                                 cudaStream_t s) {
+  const Geom& g = p->g;
+  const DevAxis* d = p->dev;
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].Tinv, in, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_DIV, d[0].lam, d[1].lam, d[2].lam, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].T, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH(p, K_F64, 1, s,
+         launch_mode_product_f64(g, 0, d[0].T, A, out, accumulate ? EPI_ACCUM : EPI_STORE, nullptr, nullptr, nullptr, s));
+  return SEM3D_OK;
+}
+
+}  // namespace
+
+extern "C" sem3d_status sem3d_solve_fp64_static(sem3d_handle h, const double* f, double* u, void* stream) {
+  if (!h || !f || !u) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  if (N > kStaticMaxDofs)
+    return fail(SEM3D_ERR_INVALID_ARG, "sem3d_solve_fp64_static: nx*ny*nz = " + std::to_string(N) +
+                                           " exceeds the static scratch limit of " + std::to_string(kStaticMaxDofs));
+  if (f < u + N && u < f + N) return fail(SEM3D_ERR_INVALID_ARG, "f and u overlap");
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != h->device) return fail(SEM3D_ERR_INVALID_ARG, "current device is not the plan's device");
+  double* base = nullptr;
+  sem3d_status st = static_scratch(cur, &base);
+  if (st != SEM3D_OK) return st;
+  // Every pass writes its whole output before anything reads it, so no part
+  // of the shared scratch has to start at zero.
+  double* A = base;
+  double* B = base + N;
+  double* r = base + 2 * N;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = solve_once_f64_into(h, f, u, false, A, B, s)) != SEM3D_OK) return st;
+  for (int sw = 0; sw < h->sweeps; ++sw) {
+    LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+    if ((st = solve_once_f64_into(h, r, u, true, A, B, s)) != SEM3D_OK) return st;
+  }
+  return SEM3D_OK;
+}

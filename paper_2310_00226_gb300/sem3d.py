@@ -37,6 +37,7 @@ EXPORTS = (
     "sem3d_profile",
     "sem3d_profile_read",
     "sem3d_launch_count",
+    "sem3d_solve_fp64_static",
     "sem3d_destroy",
     "sem3d_last_error",
 )
@@ -74,6 +75,7 @@ def lib() -> ctypes.CDLL:
     L.sem3d_profile_read.argtypes = [c_void_p, c_int, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_double)]
     L.sem3d_launch_count.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.sem3d_solve_fp64_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_destroy.argtypes = [c_void_p]
     L.sem3d_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
