@@ -264,6 +264,12 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
     std::vector<float> lf(A.lam.begin(), A.lam.end());
     if ((st = dev_upload(p.get(), &D.lamf, lf.data(), lf.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.Hband, A.Hband.data(), A.Hband.size())) != SEM3D_OK) return st;
+    {
+      std::vector<double> hq = A.Hq;  // the shift c joins the x operator's diagonal
+      if (a == 0)
+        for (int q = 0; q < k; ++q) hq[(size_t)q * (2 * k + 1) + k] += c;
+      if ((st = dev_upload(p.get(), &D.Hq, hq.data(), hq.size())) != SEM3D_OK) return st;
+    }
     if ((st = dev_upload(p.get(), &D.band_lo, A.band_lo.data(), A.band_lo.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.band_hi, A.band_hi.data(), A.band_hi.size())) != SEM3D_OK) return st;
     std::vector<__nv_bfloat16> hi, lo;

@@ -185,6 +185,123 @@ __global__ void __launch_bounds__(256) stencil_kernel(StencilArgs a) {
   }
 }
 
+// Element-wise variant of the same operator for a uniform mesh and
+// 1 <= K <= 8.  Along x, one thread owns the K global nodes g = ex*K + q
+// (q = 0..K-1) of element ex: node q = 0 is the vertex shared with element
+// ex-1 (row of 2K+1 entries), q > 0 are the element's other nodes (K+1
+// entries each).  The thread keeps the 2K+1 node values of elements ex-1 and
+// ex in registers, and every thread runs the same fully unrolled loops, so
+// the lanes of a warp never wait on each other's band lengths.  The rows of
+// H depend only on q (table Hq, x table with c added on its diagonal).  The
+// y and z bands are uniform across a warp (its lanes share j and l).
+// Work per node: k+2 FMAs per axis on average (6 at k = 4), accumulated from
+// f in residual modes.
+template <int K, int MODE>
+__global__ void __launch_bounds__(256) stencil_elem_kernel(StencilArgs a, const double* __restrict__ Hqx,
+                                                           const double* __restrict__ Hqy,
+                                                           const double* __restrict__ Hqz, int nex) {
+  constexpr int BW = 2 * K + 1;
+  const long long lines = (long long)a.ny * a.nz;
+  const long long total = (long long)nex * lines;
+  const long long plane = (long long)a.nx * a.ny;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(t % nex);
+    const long long jl = t / nex;
+    const int j = (int)(jl % a.ny), l = (int)(jl / a.ny);
+    const long long line = jl * a.nx;
+    const int i0 = ex * K - 1;  // unknown index of node q = 0 (g = ex*K)
+    // x window: global nodes (ex-1)K .. (ex+1)K -> unknowns i0-K .. i0+K
+    double w[BW];
+#pragma unroll
+    for (int d = 0; d < BW; ++d) {
+      const int i = i0 - K + d;
+      w[d] = (i >= 0 && i < a.nx) ? __ldg(a.u + line + i) : 0.0;
+    }
+    double acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int i = i0 + q;
+      acc[q] = (MODE != 0 && i >= 0) ? __ldg(a.f + line + i) : 0.0;
+    }
+    // x part
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int dlo = (q == 0) ? -K : -q, dhi = (q == 0) ? K : K - q;
+#pragma unroll
+      for (int d = dlo; d <= dhi; ++d) {
+        const double hv = __ldg(Hqx + q * BW + d + K);
+        if (MODE == 0) acc[q] += hv * w[K + q + d];
+        else acc[q] -= hv * w[K + q + d];
+      }
+    }
+    // y part: row j of H_y, local index qy = (j+1) % K
+    {
+      const int qy = (j + 1) % K;
+      const int dlo = (qy == 0) ? -K : -qy, dhi = (qy == 0) ? K : K - qy;
+      for (int d = dlo; d <= dhi; ++d) {
+        const int jj = j + d;
+        if (jj < 0 || jj >= a.ny) continue;
+        const double hv = __ldg(Hqy + qy * BW + d + K);
+        const double* src = a.u + ((long long)l * a.ny + jj) * a.nx;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int i = i0 + q;
+          const double uv = (i >= 0) ? __ldg(src + i) : 0.0;
+          if (MODE == 0) acc[q] += hv * uv;
+          else acc[q] -= hv * uv;
+        }
+      }
+    }
+    // z part
+    {
+      const int qz = (l + 1) % K;
+      const int dlo = (qz == 0) ? -K : -qz, dhi = (qz == 0) ? K : K - qz;
+      for (int d = dlo; d <= dhi; ++d) {
+        const int ll = l + d;
+        if (ll < 0 || ll >= a.nz) continue;
+        const double hv = __ldg(Hqz + qz * BW + d + K);
+        const double* src = a.u + (long long)ll * plane + (long long)j * a.nx;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int i = i0 + q;
+          const double uv = (i >= 0) ? __ldg(src + i) : 0.0;
+          if (MODE == 0) acc[q] += hv * uv;
+          else acc[q] -= hv * uv;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int i = i0 + q;
+      if (i < 0) continue;
+      if (MODE != 2) {
+        a.out64[line + i] = acc[q];
+      } else {
+        const float rf = (float)acc[q];
+        const __nv_bfloat16 h16 = __float2bfloat16_rn(rf);
+        const __nv_bfloat16 l16 = __float2bfloat16_rn(rf - __bfloat162float(h16));
+        const long long o = (long long)i + (long long)a.Px * jl;
+        a.hi[o] = h16;
+        a.lo[o] = l16;
+      }
+    }
+  }
+}
+
+template <int K>
+cudaError_t launch_elem(const StencilArgs& a, const DevAxis* ax, int mode, cudaStream_t s) {
+  const int nex = (a.nx + 1) / K;
+  const long long total = (long long)nex * a.ny * a.nz;
+  long long b = (total + 255) / 256;
+  if (b > 152LL * 64) b = 152LL * 64;
+  const int grid = (int)(b < 1 ? 1 : b);
+  if (mode == 0) stencil_elem_kernel<K, 0><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
+  else if (mode == 1) stencil_elem_kernel<K, 1><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
+  else stencil_elem_kernel<K, 2><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
+  return cudaGetLastError();
+}
+
 // Zero the pad columns i in [nx, Px) of a split array (the stencil writes
 // only i < nx).
 __global__ void zero_pads_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int nx, int Px, long long lines) {
@@ -264,8 +381,20 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
   a.loz = ax[2].band_lo; a.hiz = ax[2].band_hi;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.k = k; a.Px = g.Px; a.mode = mode; a.c = g.c;
   const long long N = (long long)g.nx * g.ny * g.nz;
-  stencil_kernel<<<grid_for(N, 256), 256, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  switch (k) {
+    case 1: e = launch_elem<1>(a, ax, mode, s); break;
+    case 2: e = launch_elem<2>(a, ax, mode, s); break;
+    case 3: e = launch_elem<3>(a, ax, mode, s); break;
+    case 4: e = launch_elem<4>(a, ax, mode, s); break;
+    case 5: e = launch_elem<5>(a, ax, mode, s); break;
+    case 6: e = launch_elem<6>(a, ax, mode, s); break;
+    case 7: e = launch_elem<7>(a, ax, mode, s); break;
+    case 8: e = launch_elem<8>(a, ax, mode, s); break;
+    default:  // higher degrees: one thread per node, per-row band ranges
+      stencil_kernel<<<grid_for(N, 256), 256, 0, s>>>(a);
+      e = cudaGetLastError();
+  }
   if (e != cudaSuccess || mode != 2 || g.Px == g.nx) return e;
   const long long lines = (long long)g.ny * g.nz;
   zero_pads_kernel<<<grid_for(lines * (g.Px - g.nx), 256), 256, 0, s>>>(out_hi, out_lo, g.nx, g.Px, lines);

@@ -27,6 +27,10 @@ struct Axis1D {
   std::vector<double> Tinv;     // n x n row-major, T^{-1}
   std::vector<double> Hband;    // n x (2k+1): H[i][i+d] at [i*(2k+1) + d + k]
   std::vector<int> band_lo, band_hi;  // nonzero column range of row i of H
+  // Uniform mesh: the row of H at global node g depends only on q = g % k.
+  // Hq[q*(2k+1) + d + k] = H[g][g+d], including the columns of the two
+  // boundary nodes (their values are zero, so those entries are never used).
+  std::vector<double> Hq;
 };
 
 void gll_rule(int N, std::vector<double>& r, std::vector<double>& w);
@@ -46,6 +50,7 @@ struct DevAxis {
   double* lam = nullptr;        // FP64 eigenvalues
   float* lamf = nullptr;        // FP32 copy for the low-precision epilogues
   double* Hband = nullptr;      // FP64 n x (2k+1)
+  double* Hq = nullptr;         // FP64 k x (2k+1) per-local-index rows of H (x axis: + c on the diagonal)
   int* band_lo = nullptr;
   int* band_hi = nullptr;
   __nv_bfloat16* W_hi[2] = {nullptr, nullptr};  // [0] = T^{-1}, [1] = T; n rows x Kp

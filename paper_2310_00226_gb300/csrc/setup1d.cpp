@@ -298,6 +298,23 @@ Axis1D build_axis(int n, int k, double L) {
     ax.band_lo[i] = lo;
     ax.band_hi[i] = hi;
   }
+  // Per-local-index rows of H on the uniform mesh, summed in the same order as
+  // the assembly above (left element first at a shared vertex), so that they
+  // equal the assembled rows bit for bit.
+  ax.Hq.assign((size_t)k * bw, 0.0);
+  for (int q = 0; q < k; ++q) {
+    const double Mq = (q == 0) ? (0.0 + h * w[k]) + h * w[0] : 0.0 + h * w[q];
+    for (int d = -k; d <= k; ++d) {
+      double sv = 0.0;
+      if (q == 0) {
+        if (d <= 0) sv += Sloc[(size_t)k * nl + (k + d)] / h;
+        if (d >= 0) sv += Sloc[(size_t)0 * nl + d] / h;
+      } else if (d >= -q && d <= k - q) {
+        sv += Sloc[(size_t)q * nl + (q + d)] / h;
+      }
+      ax.Hq[(size_t)q * bw + (d + k)] = sv / Mq;
+    }
+  }
   return ax;
 }
 
