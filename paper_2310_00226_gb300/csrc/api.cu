@@ -250,13 +250,13 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
   if (!(c > -lmin)) return fail(SEM3D_ERR_INVALID_ARG, "c <= -(lambda_x1 + lambda_y1 + lambda_z1): not definite");
   CUDA_TRY(cudaGetDevice(&p->device));
   CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
-  p->g.nx = nx; p->g.ny = ny; p->g.nz = nz; p->g.Px = pad8(nx); p->g.c = c;
+  p->g.nx = nx; p->g.ny = ny; p->g.nz = nz; p->g.Px = pad16(nx); p->g.c = c;
   p->k = k;
   for (int a = 0; a < 3; ++a) p->L[a] = L3[a];
   for (int a = 0; a < 3; ++a) {
     const Axis1D& A = *p->ax[a];
     DevAxis& D = p->dev[a];
-    D.n = A.n; D.k = k; D.Kp = pad8(A.n);
+    D.n = A.n; D.k = k; D.Kp = pad16(A.n);
     sem3d_status st;
     if ((st = dev_upload(p.get(), &D.T, A.T.data(), A.T.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.Tinv, A.Tinv.data(), A.Tinv.size())) != SEM3D_OK) return st;

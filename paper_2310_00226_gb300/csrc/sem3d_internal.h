@@ -39,12 +39,13 @@ Axis1D build_axis(int n, int k, double L);
 
 // ---------------------------------------------------------------- device data
 
-// Pitch (elements) of the x dimension of the tensor-core working arrays:
-// a multiple of 8 so that every bf16 row starts on a 16-byte boundary (TMA).
-inline int pad8(int n) { return (n + 7) & ~7; }
+// Pitch (elements) of the x dimension of the tensor-core working arrays and
+// of the bf16 matrices: a multiple of 16 so that every bf16 row starts on a
+// 32-byte boundary (TMA needs 16; 32 keeps row segments sector-aligned).
+inline int pad16(int n) { return (n + 15) & ~15; }
 
 struct DevAxis {
-  int n = 0, k = 0, Kp = 0;     // Kp = pad8(n): row pitch of the bf16 matrices
+  int n = 0, k = 0, Kp = 0;     // Kp = pad16(n): row pitch of the bf16 matrices
   double* T = nullptr;          // FP64 n x n row-major (W[out][in] for the backward pass)
   double* Tinv = nullptr;       // FP64 n x n row-major (W[out][in] for the forward pass)
   double* lam = nullptr;        // FP64 eigenvalues

@@ -8,7 +8,7 @@
 // tensor memory as A_hi W_hi + A_hi W_lo + A_lo W_hi (the dropped lo*lo term
 // is below FP32 rounding of the sum).
 //
-// Layout (bf16 working arrays, x pitch Px = pad8(nx), element (i,j,l) at
+// Layout (bf16 working arrays, x pitch Px = pad16(nx), element (i,j,l) at
 // i + Px*(j + ny*l)):
 //   x pass: rows = (j,l) lines, t = i is contiguous      -> A is K-major
 //   y pass: rows = i (contiguous), t = j, batch = l      -> A is MN-major
@@ -119,6 +119,25 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -155,6 +174,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Arrive on the mbarrier at the same offset in every CTA of `mask` once all
+// tcgen05 operations issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(bar), "h"(mask)
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -198,6 +225,18 @@ __device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uin
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(v1 - h1), "f"(v0 - h0));
 }
 
+// Exact FP32 -> FP64 conversion with integer operations (keeps the FP64 pipe,
+// ~1/64 of the FP32 rate on this GPU, free for the update's addition).
+// FP32 subnormals (|x| < 1.2e-38) become signed zero; Inf/NaN are kept.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  const uint64_t e64 = (e == 0xFFu) ? 0x7FFull : (uint64_t)(e + 896u);
+  const uint64_t bits = sign | (e64 << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)(e == 0u ? sign : bits));
+}
+
 __device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
   asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"((unsigned short)(v & 0xFFFFu)) : "memory");
 }
@@ -226,19 +265,25 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     }
     if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
       double* dst = a.out64 + (size_t)row * a.nx + col0;
+      // Loads first, 16 at a time: the read-modify-writes are independent, but
+      // the compiler cannot prove it through one pointer and would otherwise
+      // serialise one memory round trip per element.
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        if (full || col0 + q < a.nout) {
-          if (MODE == OUT_F64_ACCUM) dst[q] += (double)v[q];
-          else dst[q] = (double)v[q];
-        }
+      for (int h = 0; h < 32; h += 16) {
+        double old[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          old[q] = (MODE == OUT_F64_ACCUM && (full || col0 + h + q < a.nout)) ? dst[h + q] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (full || col0 + h + q < a.nout) dst[h + q] = old[q] + f32_to_f64(v[h + q]);
       }
     } else {
       __nv_bfloat16* dh = a.out_hi + (size_t)row * a.Px + col0;
       __nv_bfloat16* dl = a.out_lo + (size_t)row * a.Px + col0;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        if (col0 + 8 * g + 8 > a.Px) break;  // Px is a multiple of 8
+        if (col0 + 8 * g + 8 > a.Px) break;  // Px is a multiple of 16
         uint4 hh, ll;
         split_pair(v[8 * g + 0], v[8 * g + 1], hh.x, ll.x);
         split_pair(v[8 * g + 2], v[8 * g + 3], hh.y, ll.y);
@@ -280,13 +325,16 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     if (PASS == 1) { base = (size_t)i + (size_t)a.nx * a.ny * batch; cs64 = (size_t)a.nx; }
     else { base = (size_t)i + (size_t)a.nx * j; cs64 = (size_t)a.nx * a.ny; }
     double* p = a.out64 + base + (size_t)col0 * cs64;
+    // Loads first, 16 at a time (see the x pass).
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      if (full || col0 + q < a.nout) {
-        if (MODE == OUT_F64_ACCUM) *p += (double)v[q];
-        else *p = (double)v[q];
-      }
-      p += cs64;
+    for (int h = 0; h < 32; h += 16) {
+      double old[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        old[q] = (MODE == OUT_F64_ACCUM && (full || col0 + h + q < a.nout)) ? p[(size_t)(h + q) * cs64] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (full || col0 + h + q < a.nout) p[(size_t)(h + q) * cs64] = old[q] + f32_to_f64(v[h + q]);
     }
   } else {
     __nv_bfloat16* ph = a.out_hi + rowoff + (size_t)col0 * cs;
@@ -303,7 +351,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
   }
 }
 
-template <int PASS, int MODE>
+// Thread-block clusters of CL CTAs (CL = 1, 2 or 4) work on CL consecutive M
+// tiles that share one N tile, so they need the same W tile: each CTA loads
+// BN/CL of its rows and multicasts them into the shared memory of all CL CTAs,
+// which cuts the L2 -> SM traffic of W (2/3 of all operand traffic at
+// BM = 128, BN = 256) by CL.  A stage may be refilled only when every CTA of
+// the cluster has finished the MMAs that read it: each CTA's MMA completion
+// arrives on the "empty" barrier of all CL CTAs (count CL).
+template <int PASS, int MODE, int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -319,12 +374,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+  constexpr int WROWS = BN / CL;  // rows of the W tile this CTA loads
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool a_mn = (PASS != 0);
+  const int rank = (CL > 1) ? (int)cluster_ctarank() : 0;
+  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+    for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), CL); }
     for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), EPI_WARPS); }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -337,21 +396,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync_all();  // peers' barriers are initialised before any multicast
   tc_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
 
-  const int tiles_per_batch = a.m_tiles * a.n_tiles;
-  const int total_tiles = tiles_per_batch * a.batches;
+  // Cluster tile ct -> (batch b, M group mg, N tile nt); this CTA's M tile is
+  // mg*CL + rank (it may lie past the last M tile: TMA then reads zeros and
+  // the epilogue stores nothing).
+  const int m_groups = (a.m_tiles + CL - 1) / CL;
+  const int tiles_per_batch = m_groups * a.n_tiles;
+  const int total_ct = tiles_per_batch * a.batches;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------ TMA producer
     int it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-      const int b = t / tiles_per_batch;
-      const int rem = t - b * tiles_per_batch;
-      const int mt = rem / a.n_tiles, nt = rem - mt * a.n_tiles;
-      const int m0 = mt * BM, n0 = nt * BN;
+    for (int ct = cid; ct < total_ct && ok; ct += ncl) {
+      const int b = ct / tiles_per_batch;
+      const int rem = ct - b * tiles_per_batch;
+      const int mg = rem / a.n_tiles, nt = rem - mg * a.n_tiles;
+      const int m0 = (mg * CL + rank) * BM, n0 = nt * BN;
       for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t par = ((it / STAGES) & 1) ^ 1;
@@ -375,14 +439,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tma_load_2d(a_lo, &tmA_lo, full_bar(s), m0, k0);
           tma_load_2d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0);
         }
-        tma_load_2d(b_hi, &tmB_hi, full_bar(s), k0, n0);
-        tma_load_2d(b_lo, &tmB_lo, full_bar(s), k0, n0);
+        const uint32_t woff = (uint32_t)(rank * WROWS * BK * 2);
+        if (CL == 1) {
+          tma_load_2d(b_hi, &tmB_hi, full_bar(s), k0, n0);
+          tma_load_2d(b_lo, &tmB_lo, full_bar(s), k0, n0);
+        } else {
+          tma_load_2d_mc(b_hi + woff, &tmB_hi, full_bar(s), k0, n0 + rank * WROWS, kMask);
+          tma_load_2d_mc(b_lo + woff, &tmB_lo, full_bar(s), k0, n0 + rank * WROWS, kMask);
+        }
       }
     }
-    // Drain: every stage this thread armed must have landed before exit.
+    // Drain: every stage this thread armed must have landed, and (clusters)
+    // every CTA must have released the last fill of each stage, so that no
+    // copy or remote arrival targets this CTA after it exits.
     const int armed = it;
-    for (int q = (armed > STAGES ? armed - STAGES : 0); q < armed; ++q)
+    for (int q = (armed > STAGES ? armed - STAGES : 0); q < armed; ++q) {
       mbar_wait(full_bar(q % STAGES), (q / STAGES) & 1, nullptr);
+      if (CL > 1) mbar_wait(empty_bar(q % STAGES), (q / STAGES) & 1, nullptr);
+    }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer
     constexpr uint32_t idesc = make_idesc(BM, BN, a_mn);
@@ -395,7 +469,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     constexpr uint32_t a_layout = a_mn ? LAYOUT_SW128 : LAYOUT_SW64;
     int it = 0, tl = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++tl) {
+    for (int ct = cid; ct < total_ct && ok; ct += ncl, ++tl) {
       const int buf = tl & 1;
       if (!mbar_wait(tempty_bar(buf), ((tl >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
       tc_fence_after();
@@ -418,7 +492,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           mma_bf16(tmem_d, dah, dbl, idesc, 1u);
           mma_bf16(tmem_d, dal, dbh, idesc, 1u);
         }
-        mma_commit(empty_bar(s));  // frees the smem stage when these MMAs finish
+        // The stage is free (in every CTA of the cluster) once these MMAs finish.
+        if (CL == 1) mma_commit(empty_bar(s));
+        else mma_commit_mc(empty_bar(s), kMask);
       }
       if (!ok) break;
       mma_commit(tfull_bar(buf));  // accumulator ready for the epilogue
@@ -434,20 +510,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int slice = (warp - 2) >> 2;
     constexpr int COLS = BN / (EPI_WARPS / 4);
     int tl = 0;
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++tl) {
+    for (int ct = cid; ct < total_ct; ct += ncl, ++tl) {
       const int buf = tl & 1;
       if (!mbar_wait(tfull_bar(buf), (tl >> 1) & 1, a.err)) break;
       tc_fence_after();
-      const int b = t / tiles_per_batch;
-      const int rem = t - b * tiles_per_batch;
-      const int mt = rem / a.n_tiles, nt = rem - mt * a.n_tiles;
+      const int b = ct / tiles_per_batch;
+      const int rem = ct - b * tiles_per_batch;
+      const int mg = rem / a.n_tiles, nt = rem - mg * a.n_tiles;
+      const int mt = mg * CL + rank;
       const int row = mt * BM + quad * 32 + lane;
       const uint32_t taddr =
           tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + slice * COLS);
 #pragma unroll 1
       for (int ch = 0; ch < COLS / 32; ++ch) {
         const int col0 = nt * BN + slice * COLS + ch * 32;
-        if (col0 >= a.nout) break;  // warp-uniform
+        if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
         float v[32];
         tmem_ld32(taddr + ch * 32, v);
         epilogue_chunk<PASS, MODE>(a, row, col0, b, v);
@@ -460,6 +537,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncwarp();
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync_all();  // no peer copy or arrival can target this CTA any more
   tc_fence_after();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS));
@@ -500,28 +578,65 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, 
 
 namespace {
 
+// Cluster size of the W multicast (1 = none).
+#ifndef SEM3D_TC_CLUSTER
+#define SEM3D_TC_CLUSTER 4
+#endif
+constexpr int CLUSTER = SEM3D_TC_CLUSTER;
+
 template <int PASS, int MODE>
 cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
-                      const TcArgs& a, int grid, cudaStream_t s) {
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mode_product_bf16x3_kernel<PASS, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+                      const TcArgs& a, long long work_clusters, int num_sms, cudaStream_t s) {
+  auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER>;
+  static int max_clusters = 0;  // per instantiation: co-resident clusters of CLUSTER CTAs
+  if (max_clusters == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (CLUSTER > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CLUSTER;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(CLUSTER * (num_sms / CLUSTER));
+      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.dynamicSmemBytes = SMEM_BYTES;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      if (n < 1) return cudaErrorInvalidConfiguration;
+      max_clusters = n;
+    } else {
+      max_clusters = num_sms;
+    }
   }
-  mode_product_bf16x3_kernel<PASS, MODE><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(a0, a1, b0, b1, a);
-  return cudaGetLastError();
+  const long long clusters = work_clusters < max_clusters ? work_clusters : max_clusters;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(clusters * CLUSTER));
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a0, a1, b0, b1, a);
 }
 
 template <int PASS>
 cudaError_t launch_tc_mode(int mode, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
-                           const CUtensorMap& b1, const TcArgs& a, int grid, cudaStream_t s) {
+                           const CUtensorMap& b1, const TcArgs& a, long long work, int num_sms, cudaStream_t s) {
   switch (mode) {
-    case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT>(a0, a1, b0, b1, a, grid, s);
-    case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT>(a0, a1, b0, b1, a, grid, s);
-    case OUT_F64: return launch_tc<PASS, OUT_F64>(a0, a1, b0, b1, a, grid, s);
-    default: return launch_tc<PASS, OUT_F64_ACCUM>(a0, a1, b0, b1, a, grid, s);
+    case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_F64: return launch_tc<PASS, OUT_F64>(a0, a1, b0, b1, a, work, num_sms, s);
+    default: return launch_tc<PASS, OUT_F64_ACCUM>(a0, a1, b0, b1, a, work, num_sms, s);
   }
 }
 
@@ -571,10 +686,10 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
     a.rows = g.Px * g.ny; a.batches = 1; nin = g.nz;
   }
   {
-    // W: dims {t: n, o: n}, row pitch Kp*2 B; box {BK (K), 256 rows}
+    // W: dims {t: n, o: n}, row pitch Kp*2 B; box {BK (K), BN/CLUSTER rows}
     const uint64_t dims[2] = {(uint64_t)W.n, (uint64_t)W.n};
     const uint64_t str[1] = {(uint64_t)W.Kp * 2};
-    const uint32_t box[2] = {BK, (uint32_t)BN};
+    const uint32_t box[2] = {BK, (uint32_t)(BN / CLUSTER)};
     ok = ok && make_map(&mBh, W.W_hi[which], 2, dims, str, box, SWZ_K) &&
          make_map(&mBl, W.W_lo[which], 2, dims, str, box, SWZ_K);
   }
@@ -583,12 +698,11 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   a.m_tiles = (a.rows + BM - 1) / BM;
   a.n_tiles = (W.n + BN - 1) / BN;
   a.k_blocks = (nin + BK - 1) / BK;
-  const long long total = (long long)a.m_tiles * a.n_tiles * a.batches;
-  if (total >= (1LL << 31)) return cudaErrorInvalidValue;
-  const int grid = (int)(total < num_sms ? total : num_sms);
-  if (axis == 0) return launch_tc_mode<0>(mode, mAh, mAl, mBh, mBl, a, grid, s);
-  if (axis == 1) return launch_tc_mode<1>(mode, mAh, mAl, mBh, mBl, a, grid, s);
-  return launch_tc_mode<2>(mode, mAh, mAl, mBh, mBl, a, grid, s);
+  const long long work = (long long)((a.m_tiles + CLUSTER - 1) / CLUSTER) * a.n_tiles * a.batches;
+  if (work >= (1LL << 31)) return cudaErrorInvalidValue;
+  if (axis == 0) return launch_tc_mode<0>(mode, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  if (axis == 1) return launch_tc_mode<1>(mode, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  return launch_tc_mode<2>(mode, mAh, mAl, mBh, mBl, a, work, num_sms, s);
 }
 
 }  // namespace sem3d
