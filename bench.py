@@ -202,6 +202,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # ---- headline: BF16x3 + FP64 refinement sweeps
     plan.set_precision("bf16x3", args.sweeps)
+    plan.set_residual(args.residual)
     step = lambda: plan.solve(f, u, stream)  # noqa: E731
     for _ in range(args.warmup):
         step()
@@ -232,6 +233,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     plan.apply(u_bf, Au, stream)
     rel_res = float((f - Au).abs().max() / f.abs().max())
     del Au
+
+    # ---- the same BF16x3 path with FP64 residuals in every sweep
+    f64res = None
+    if args.fp64_residual_steps > 0:
+        plan.set_residual("fp64")
+        ms_r = timed(step, args.fp64_residual_steps, 1, stream, torch, dist)
+        plan.sync_check(stream)
+        f64res = {"ms_per_step": ms_r, "value": dofs * world / (ms_r / 1e3) / 1e9, "unit": "GDoF/s",
+                  "steps": args.fp64_residual_steps, "warmup": 1,
+                  "rel_linf_vs_mixed": float((u - u_bf).abs().max() / u_bf.abs().max())}
+        plan.set_residual(args.residual)
 
     # ---- plain FP64 DMMA path (+1 FP64 sweep)
     fp64 = None
@@ -297,12 +309,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate) + f64 refinement", "data": "synthetic",
         "config": {"workload": f"q4_n{n}_expsine: Q^4, Ne={(n + 1) // k}/axis on [0,1]^3, n={n}, {dofs} DoF, "
                                "-Lap u + u = f, u = e^x sin(pi x) sin(pi y) sin(pi z), Dirichlet",
-                   "path": f"tcgen05 BF16x3 mode products + {args.sweeps} FP64 refinement sweeps",
+                   "path": (f"tcgen05 BF16x3 mode products + {args.sweeps} refinement sweeps; residuals: "
+                            + ("double-FP32 except the last, FP64" if args.residual == "mixed" else "FP64")),
                    "l2": "inputs larger than L2 (8 GB FP64 per array, 4 GB split-bf16 per pass)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": t_setup},
         "accuracy": {"rel_linf_vs_exact_solution": err_exact, "rel_residual_linf": rel_res},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
-        "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu,
+        "fp64_path": fp64, "bf16x3_fp64_residuals": f64res, "e2e": e2e, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -320,6 +333,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=999, help="interior nodes per axis (n+1 divisible by 4)")
     ap.add_argument("--sweeps", type=int, default=3)
+    ap.add_argument("--residual", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--fp64-residual-steps", type=int, default=3,
+                    help="also time the BF16x3 path with FP64 residuals in every sweep (0 = skip)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

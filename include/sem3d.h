@@ -85,6 +85,21 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
  * With a fixed sweep count the solve performs no host synchronisation. */
 sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
 
+/* Arithmetic of the refinement residuals in the SEM3D_BF16X3 tier.
+ *   SEM3D_RESIDUAL_FP64  : every sweep computes r = f - (c + H_x (+) H_y (+)
+ *                          H_z) u in FP64 with the banded operator of Eq. 12.
+ *   SEM3D_RESIDUAL_MIXED : (default) sweeps 1 .. s-1 compute it in double-FP32
+ *                          arithmetic (pairs of FP32 numbers, ~48 significant
+ *                          bits; products by the FMA error-free transform)
+ *                          with the solution held as a double-FP32 pair; the
+ *                          last sweep computes it in FP64 on the FP64
+ *                          solution.  The final accuracy is that of the last
+ *                          (FP64) residual.  Applies for k <= 8 and s >= 2;
+ *                          otherwise every sweep is FP64.
+ * The FP64 tier always uses FP64 residuals. */
+typedef enum { SEM3D_RESIDUAL_FP64 = 0, SEM3D_RESIDUAL_MIXED = 1 } sem3d_residual;
+sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode);
+
 /* Bytes of device workspace that sem3d_solve needs in the current mode. */
 sem3d_status sem3d_workspace_size(sem3d_handle h, size_t* bytes);
 

@@ -65,6 +65,7 @@ struct sem3d_plan {
   DevAxis dev[3];
   sem3d_precision prec = SEM3D_FP64;
   int sweeps = 1;
+  int residual = SEM3D_RESIDUAL_MIXED;  // arithmetic of the refinement residuals (BF16X3 tier)
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -157,12 +158,13 @@ struct LaunchScope {
 
 // Workspace layout per mode.
 //   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
-//   BF16X3 : two split arrays {hi, lo} of Px*ny*nz bf16 each.
+//   BF16X3 : two split arrays {hi, lo} of Px*ny*nz bf16 each, and the
+//            double-FP32 solution (two FP32 n^3 arrays) used between sweeps.
 size_t workspace_bytes(const sem3d_plan* p) {
   const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
   if (p->prec == SEM3D_FP64) return 3 * align256(N * sizeof(double));
   const size_t Ns = (size_t)p->g.Px * p->g.ny * p->g.nz;
-  return 4 * align256(Ns * sizeof(__nv_bfloat16));
+  return 4 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(N * sizeof(float));
 }
 
 sem3d_status ensure_workspace(sem3d_plan* p) {
@@ -197,8 +199,10 @@ sem3d_status solve_once_f64(sem3d_plan* p, const double* in, double* out, bool a
   return SEM3D_OK;
 }
 
-// ---- BF16x3 path: the split input is in buffer S0; result into FP64 out.
-sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double* out, bool accumulate,
+// ---- BF16x3 path: the split input is in buffer S0.  The last (z) pass
+// writes the result with epilogue `epi_last` into out64 and/or the
+// double-FP32 solution df.
+sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double* out64, int epi_last, DfBuffers df,
                                cudaStream_t s) {
   const Geom& g = p->g;
   const DevAxis* d = p->dev;
@@ -211,11 +215,11 @@ sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double
   LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
   // Backward: x, y, z.  The mode products commute, so the order is free; the
   // z pass goes last because its TMEM lanes run along the contiguous index,
-  // which makes the FP64 read-modify-write of u coalesced.
+  // which makes the read-modify-write of the solution coalesced.
   LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
   LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH_SUB(p, K_TC, K_TC_F64OUT, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out, accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz,
-                                      e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_F64OUT, 1, s,
+             launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out64, epi_last, lx, ly, lz, e, sms, s, df));
   return SEM3D_OK;
 }
 
@@ -269,6 +273,13 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
       if (a == 0)
         for (int q = 0; q < k; ++q) hq[(size_t)q * (2 * k + 1) + k] += c;
       if ((st = dev_upload(p.get(), &D.Hq, hq.data(), hq.size())) != SEM3D_OK) return st;
+      std::vector<float> hh(hq.size()), hl(hq.size());
+      for (size_t q = 0; q < hq.size(); ++q) {
+        hh[q] = (float)hq[q];
+        hl[q] = (float)(hq[q] - (double)hh[q]);
+      }
+      if ((st = dev_upload(p.get(), &D.Hq_hi, hh.data(), hh.size())) != SEM3D_OK) return st;
+      if ((st = dev_upload(p.get(), &D.Hq_lo, hl.data(), hl.size())) != SEM3D_OK) return st;
     }
     if ((st = dev_upload(p.get(), &D.band_lo, A.band_lo.data(), A.band_lo.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.band_hi, A.band_hi.data(), A.band_hi.size())) != SEM3D_OK) return st;
@@ -305,6 +316,13 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweep
   return SEM3D_OK;
 }
 
+sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  if (mode != SEM3D_RESIDUAL_FP64 && mode != SEM3D_RESIDUAL_MIXED) return fail(SEM3D_ERR_INVALID_ARG, "unknown mode");
+  h->residual = mode;
+  return SEM3D_OK;
+}
+
 sem3d_status sem3d_workspace_size(sem3d_handle h, size_t* bytes) {
   if (!h || !bytes) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
   *bytes = workspace_bytes(h);
@@ -338,15 +356,34 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
     }
   } else {
     const size_t Ns = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(__nv_bfloat16));
+    const size_t Nf = align256(N * sizeof(float));
     char* w = static_cast<char*>(h->ws);
     TcBuffers S0{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
     TcBuffers S1{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
+    DfBuffers D{reinterpret_cast<float*>(w + 4 * Ns), reinterpret_cast<float*>(w + 4 * Ns + Nf)};
+    const DfBuffers none{nullptr, nullptr};
+    const int sw = h->sweeps;
+    // Mixed residuals: sweeps 1 .. sw-1 in double-FP32 with the solution held
+    // as a double-FP32 pair, the last sweep in FP64 on the FP64 solution.
+    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8;
     LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s));
-    if ((st = solve_once_bf16x3(h, S0, S1, u, false, s)) != SEM3D_OK) return st;
-    for (int sw = 0; sw < h->sweeps; ++sw) {
+    if (!mixed) {
+      if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_STORE, none, s)) != SEM3D_OK) return st;
+    } else {
+      if ((st = solve_once_bf16x3(h, S0, S1, nullptr, EPI_DF_STORE, D, s)) != SEM3D_OK) return st;
+      for (int q = 1; q < sw; ++q) {
+        LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
+               launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
+        const bool last_df = (q == sw - 1);
+        if ((st = solve_once_bf16x3(h, S0, S1, last_df ? u : nullptr, last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, D,
+                                    s)) != SEM3D_OK)
+          return st;
+      }
+    }
+    for (int q = mixed ? sw - 1 : 0; q < sw; ++q) {
       LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
              launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
-      if ((st = solve_once_bf16x3(h, S0, S1, u, true, s)) != SEM3D_OK) return st;
+      if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_ACCUM, none, s)) != SEM3D_OK) return st;
     }
   }
   return SEM3D_OK;

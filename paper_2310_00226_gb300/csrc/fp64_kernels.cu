@@ -302,6 +302,144 @@ cudaError_t launch_elem(const StencilArgs& a, const DevAxis* ax, int mode, cudaS
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ double-FP32 residual
+//
+// The same element-wise operator evaluated in double-FP32 arithmetic: every
+// value is a pair hi + lo of FP32 numbers (about 48 significant bits).  FP32
+// runs at ~70x the FP64 rate on this GPU, so a refinement sweep whose only
+// job is to bring the error down to the level the final FP64 sweep removes
+// can use it.  Products use the FMA error-free transformation
+// (p = a*b, e = fma(a, b, -p)), sums the two-sum of the leading parts.
+
+// Exact split of an FP64 value into hi (first 24 significant bits, truncated)
+// and lo (the next 24, rounded) with integer operations only.  |x| < 2^-126
+// gives (0, 0); 2^-126 <= |x| < 2^-74 gives lo = 0.
+__device__ __forceinline__ void f64_to_df(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126) { hi = 0.f; lo = 0.f; return; }
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29));
+  if (e < -74) { lo = 0.f; return; }
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);  // value rem * 2^(e-52)
+  const float scale = __uint_as_float((unsigned int)(e - 52 + 127) << 23);
+  lo = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) | sign);
+}
+
+// (ah, al) -= (ch + cl) * (uh + ul), dropping cl*ul.
+__device__ __forceinline__ void df_sub_prod(float& ah, float& al, float ch, float cl, float uh, float ul) {
+  const float p = ch * uh;
+  const float e = fmaf(ch, uh, -p);
+  const float t = fmaf(ch, ul, fmaf(cl, uh, e));
+  const float s = ah - p;
+  const float bb = s - ah;
+  const float err = (ah - (s - bb)) - (p + bb);
+  ah = s;
+  al = al + (err - t);
+}
+
+struct DfArgs {
+  const float* uh;
+  const float* ul;
+  const double* f;
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  const float *Hxh, *Hxl, *Hyh, *Hyl, *Hzh, *Hzl;
+  int nx, ny, nz, Px, nex;
+};
+
+template <int K>
+__global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
+  constexpr int BW = 2 * K + 1;
+  const long long lines = (long long)a.ny * a.nz;
+  const long long total = (long long)a.nex * lines;
+  const long long plane = (long long)a.nx * a.ny;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(t % a.nex);
+    const long long jl = t / a.nex;
+    const int j = (int)(jl % a.ny), l = (int)(jl / a.ny);
+    const long long line = jl * a.nx;
+    const int i0 = ex * K - 1;
+    float wh[BW], wl[BW];
+#pragma unroll
+    for (int d = 0; d < BW; ++d) {
+      const int i = i0 - K + d;
+      const bool ok = i >= 0 && i < a.nx;
+      wh[d] = ok ? __ldg(a.uh + line + i) : 0.f;
+      wl[d] = ok ? __ldg(a.ul + line + i) : 0.f;
+    }
+    float ah[K], al[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int i = i0 + q;
+      if (i >= 0) f64_to_df(__ldg(a.f + line + i), ah[q], al[q]);
+      else { ah[q] = 0.f; al[q] = 0.f; }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int dlo = (q == 0) ? -K : -q, dhi = (q == 0) ? K : K - q;
+#pragma unroll
+      for (int d = dlo; d <= dhi; ++d)
+        df_sub_prod(ah[q], al[q], __ldg(a.Hxh + q * BW + d + K), __ldg(a.Hxl + q * BW + d + K), wh[K + q + d],
+                    wl[K + q + d]);
+    }
+    {
+      const int qy = (j + 1) % K;
+      const int dlo = (qy == 0) ? -K : -qy, dhi = (qy == 0) ? K : K - qy;
+      for (int d = dlo; d <= dhi; ++d) {
+        const int jj = j + d;
+        if (jj < 0 || jj >= a.ny) continue;
+        const float ch = __ldg(a.Hyh + qy * BW + d + K), cl = __ldg(a.Hyl + qy * BW + d + K);
+        const long long off = ((long long)l * a.ny + jj) * a.nx;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int i = i0 + q;
+          if (i < 0) continue;
+          df_sub_prod(ah[q], al[q], ch, cl, __ldg(a.uh + off + i), __ldg(a.ul + off + i));
+        }
+      }
+    }
+    {
+      const int qz = (l + 1) % K;
+      const int dlo = (qz == 0) ? -K : -qz, dhi = (qz == 0) ? K : K - qz;
+      for (int d = dlo; d <= dhi; ++d) {
+        const int ll = l + d;
+        if (ll < 0 || ll >= a.nz) continue;
+        const float ch = __ldg(a.Hzh + qz * BW + d + K), cl = __ldg(a.Hzl + qz * BW + d + K);
+        const long long off = (long long)ll * plane + (long long)j * a.nx;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int i = i0 + q;
+          if (i < 0) continue;
+          df_sub_prod(ah[q], al[q], ch, cl, __ldg(a.uh + off + i), __ldg(a.ul + off + i));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int i = i0 + q;
+      if (i < 0) continue;
+      const float rf = ah[q] + al[q];
+      const __nv_bfloat16 h16 = __float2bfloat16_rn(rf);
+      const __nv_bfloat16 l16 = __float2bfloat16_rn(rf - __bfloat162float(h16));
+      const long long o = (long long)i + (long long)a.Px * jl;
+      a.hi[o] = h16;
+      a.lo[o] = l16;
+    }
+  }
+}
+
+template <int K>
+cudaError_t launch_df(const DfArgs& a, cudaStream_t s) {
+  const long long total = (long long)a.nex * a.ny * a.nz;
+  long long b = (total + 255) / 256;
+  if (b > 152LL * 64) b = 152LL * 64;
+  stencil_df_kernel<K><<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 // Zero the pad columns i in [nx, Px) of a split array (the stencil writes
 // only i < nx).
 __global__ void zero_pads_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int nx, int Px, long long lines) {
@@ -396,6 +534,33 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
       e = cudaGetLastError();
   }
   if (e != cudaSuccess || mode != 2 || g.Px == g.nx) return e;
+  const long long lines = (long long)g.ny * g.nz;
+  zero_pads_kernel<<<grid_for(lines * (g.Px - g.nx), 256), 256, 0, s>>>(out_hi, out_lo, g.nx, g.Px, lines);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
+                              __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s) {
+  DfArgs a{};
+  a.uh = u.hi; a.ul = u.lo; a.f = f; a.hi = out_hi; a.lo = out_lo;
+  a.Hxh = ax[0].Hq_hi; a.Hxl = ax[0].Hq_lo;
+  a.Hyh = ax[1].Hq_hi; a.Hyl = ax[1].Hq_lo;
+  a.Hzh = ax[2].Hq_hi; a.Hzl = ax[2].Hq_lo;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
+  a.nex = (g.nx + 1) / k;
+  cudaError_t e;
+  switch (k) {
+    case 1: e = launch_df<1>(a, s); break;
+    case 2: e = launch_df<2>(a, s); break;
+    case 3: e = launch_df<3>(a, s); break;
+    case 4: e = launch_df<4>(a, s); break;
+    case 5: e = launch_df<5>(a, s); break;
+    case 6: e = launch_df<6>(a, s); break;
+    case 7: e = launch_df<7>(a, s); break;
+    case 8: e = launch_df<8>(a, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess || g.Px == g.nx) return e;
   const long long lines = (long long)g.ny * g.nz;
   zero_pads_kernel<<<grid_for(lines * (g.Px - g.nx), 256), 256, 0, s>>>(out_hi, out_lo, g.nx, g.Px, lines);
   return cudaGetLastError();

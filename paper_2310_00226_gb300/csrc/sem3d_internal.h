@@ -52,6 +52,8 @@ struct DevAxis {
   float* lamf = nullptr;        // FP32 copy for the low-precision epilogues
   double* Hband = nullptr;      // FP64 n x (2k+1)
   double* Hq = nullptr;         // FP64 k x (2k+1) per-local-index rows of H (x axis: + c on the diagonal)
+  float* Hq_hi = nullptr;       // the same table as a double-FP32 pair: Hq = Hq_hi + Hq_lo
+  float* Hq_lo = nullptr;
   int* band_lo = nullptr;
   int* band_hi = nullptr;
   __nv_bfloat16* W_hi[2] = {nullptr, nullptr};  // [0] = T^{-1}, [1] = T; n rows x Kp
@@ -62,7 +64,16 @@ struct DevAxis {
 enum Epi : int {
   EPI_STORE = 0,       // out = acc
   EPI_DIV = 1,         // out = acc / (lam_x,i + lam_y,j + lam_z,l + c)
-  EPI_ACCUM = 2        // out += acc (FP64 outputs only)
+  EPI_ACCUM = 2,       // out += acc (FP64 outputs only)
+  EPI_DF_STORE = 3,    // double-FP32 solution (hi, lo) = (acc, 0)            [z pass]
+  EPI_DF_ACCUM = 4,    // (hi, lo) += acc                                     [z pass]
+  EPI_DF_ACCUM_F64 = 5 // FP64 out = (hi, lo) + acc                           [z pass]
+};
+
+// Solution in double-FP32 form between refinement sweeps: u = hi + lo.
+struct DfBuffers {
+  float* hi;
+  float* lo;
 };
 
 // Grid geometry of one solve.
@@ -83,6 +94,12 @@ cudaError_t launch_mode_product_f64(const Geom& g, int axis, const double* W, co
 // r  = same, written as bf16 hi/lo at pitch Px   (mode 2)
 cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f, double* out64,
                            __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int mode, cudaStream_t s);
+// r = f - (c + H_x (+) H_y (+) H_z) u in double-FP32 arithmetic (about 48
+// significant bits), u given as a double-FP32 pair, f as FP64; r written as
+// bf16 hi/lo at pitch Px.  Needs 1 <= k <= 8 (returns cudaErrorInvalidValue
+// otherwise).
+cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
+                              __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s);
 // FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads.
 cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 
@@ -98,6 +115,7 @@ struct TcPassPlan;
 // dense n-pitch array out64 (EPI_STORE / EPI_ACCUM).
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
-                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s);
+                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
+                                       DfBuffers df = DfBuffers{nullptr, nullptr});
 
 }  // namespace sem3d

@@ -209,13 +209,22 @@ struct TcArgs {
   __nv_bfloat16* out_hi;
   __nv_bfloat16* out_lo;
   double* out64;
+  float* df_hi;        // solution in double-FP32 form (hi + lo), dense n-pitch
+  float* df_lo;
   const float *lamx, *lamy, *lamz;
   float c;
   int* err;
 };
 
-// Output modes of the epilogue.
-enum : int { OUT_SPLIT = 0, OUT_DIV_SPLIT = 1, OUT_F64 = 2, OUT_F64_ACCUM = 3 };
+// Output modes of the epilogue.  The DF modes (y and z passes only) keep the
+// solution as a double-FP32 pair u = hi + lo between refinement sweeps:
+//   OUT_DF_STORE     : (hi, lo) = (acc, 0)
+//   OUT_DF_ACCUM     : (hi, lo) += acc           (compensated FP32 addition)
+//   OUT_DF_ACCUM_F64 : out64 = (double)hi + (double)lo, (hi, lo) = (hi, lo) + acc
+enum : int {
+  OUT_SPLIT = 0, OUT_DIV_SPLIT = 1, OUT_F64 = 2, OUT_F64_ACCUM = 3,
+  OUT_DF_STORE = 4, OUT_DF_ACCUM = 5, OUT_DF_ACCUM_F64 = 6
+};
 
 // Split two FP32 values into bf16 hi + lo pairs (packed bf16x2: element 0 in
 // the low half).  hi = rn(v), lo = rn(v - hi).
@@ -319,7 +328,46 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
       v[q] = __fdividef(v[q], d);
     }
   }
-  if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
+  if (MODE == OUT_DF_STORE || MODE == OUT_DF_ACCUM || MODE == OUT_DF_ACCUM_F64) {
+    if (i >= a.nx) return;
+    size_t base, cs64;
+    if (PASS == 1) { base = (size_t)i + (size_t)a.nx * a.ny * batch; cs64 = (size_t)a.nx; }
+    else { base = (size_t)i + (size_t)a.nx * j; cs64 = (size_t)a.nx * a.ny; }
+    const size_t o0 = base + (size_t)col0 * cs64;
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      float oh[16], ol[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const bool ok = full || col0 + h + q < a.nout;
+        oh[q] = (MODE != OUT_DF_STORE && ok) ? a.df_hi[o0 + (size_t)(h + q) * cs64] : 0.f;
+        ol[q] = (MODE != OUT_DF_STORE && ok) ? a.df_lo[o0 + (size_t)(h + q) * cs64] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (!(full || col0 + h + q < a.nout)) continue;
+        const size_t o = o0 + (size_t)(h + q) * cs64;
+        if (MODE == OUT_DF_STORE) {
+          a.df_hi[o] = v[h + q];
+          a.df_lo[o] = 0.f;
+        } else {
+          // (oh + ol) + v: two-sum of the leading parts, then renormalise.
+          const float sum = oh[q] + v[h + q];
+          const float bb = sum - oh[q];
+          const float err = (oh[q] - (sum - bb)) + (v[h + q] - bb);
+          const float t = ol[q] + err;
+          const float nh = sum + t;
+          const float nl = t - (nh - sum);
+          if (MODE == OUT_DF_ACCUM) {
+            a.df_hi[o] = nh;
+            a.df_lo[o] = nl;
+          } else {
+            a.out64[o] = f32_to_f64(nh) + f32_to_f64(nl);
+          }
+        }
+      }
+    }
+  } else if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
     if (i >= a.nx) return;
     size_t base, cs64;
     if (PASS == 1) { base = (size_t)i + (size_t)a.nx * a.ny * batch; cs64 = (size_t)a.nx; }
@@ -636,7 +684,14 @@ cudaError_t launch_tc_mode(int mode, const CUtensorMap& a0, const CUtensorMap& a
     case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT>(a0, a1, b0, b1, a, work, num_sms, s);
     case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT>(a0, a1, b0, b1, a, work, num_sms, s);
     case OUT_F64: return launch_tc<PASS, OUT_F64>(a0, a1, b0, b1, a, work, num_sms, s);
-    default: return launch_tc<PASS, OUT_F64_ACCUM>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_F64_ACCUM: return launch_tc<PASS, OUT_F64_ACCUM>(a0, a1, b0, b1, a, work, num_sms, s);
+    default:
+      if constexpr (PASS == 2) {
+        if (mode == OUT_DF_STORE) return launch_tc<PASS, OUT_DF_STORE>(a0, a1, b0, b1, a, work, num_sms, s);
+        if (mode == OUT_DF_ACCUM) return launch_tc<PASS, OUT_DF_ACCUM>(a0, a1, b0, b1, a, work, num_sms, s);
+        return launch_tc<PASS, OUT_DF_ACCUM_F64>(a0, a1, b0, b1, a, work, num_sms, s);
+      }
+      return cudaErrorInvalidValue;
   }
 }
 
@@ -649,12 +704,21 @@ static constexpr CUtensorMapSwizzle SWZ_MN = CU_TENSOR_MAP_SWIZZLE_128B;
 
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
-                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s) {
+                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
+                                       DfBuffers df) {
   int mode;
-  if (out64) mode = (epi == EPI_ACCUM) ? OUT_F64_ACCUM : OUT_F64;
-  else mode = (epi == EPI_DIV) ? OUT_DIV_SPLIT : OUT_SPLIT;
+  if (epi == EPI_DF_STORE || epi == EPI_DF_ACCUM || epi == EPI_DF_ACCUM_F64) {
+    if (axis != 2 || !df.hi || !df.lo || (epi == EPI_DF_ACCUM_F64 && !out64)) return cudaErrorInvalidValue;
+    mode = epi == EPI_DF_STORE ? OUT_DF_STORE : (epi == EPI_DF_ACCUM ? OUT_DF_ACCUM : OUT_DF_ACCUM_F64);
+  } else if (out64) {
+    mode = (epi == EPI_ACCUM) ? OUT_F64_ACCUM : OUT_F64;
+  } else {
+    mode = (epi == EPI_DIV) ? OUT_DIV_SPLIT : OUT_SPLIT;
+  }
   if (out64 && epi == EPI_DIV) return cudaErrorInvalidValue;
   TcArgs a{};
+  a.df_hi = df.hi;
+  a.df_lo = df.lo;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
   a.out_hi = out.hi; a.out_lo = out.lo; a.out64 = out64;
   a.lamx = lamx; a.lamy = lamy; a.lamz = lamz; a.c = (float)g.c;

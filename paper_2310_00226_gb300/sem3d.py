@@ -26,6 +26,7 @@ PRECISIONS = {"fp64": 0, "bf16x3": 5}
 EXPORTS = (
     "sem3d_setup",
     "sem3d_set_precision",
+    "sem3d_set_residual",
     "sem3d_workspace_size",
     "sem3d_set_workspace",
     "sem3d_solve",
@@ -63,6 +64,7 @@ def lib() -> ctypes.CDLL:
     L.sem3d_setup.argtypes = [c_int, c_int, c_int, c_int, c_double, c_double, c_double, c_double,
                               ctypes.POINTER(c_void_p)]
     L.sem3d_set_precision.argtypes = [c_void_p, c_int, c_int]
+    L.sem3d_set_residual.argtypes = [c_void_p, c_int]
     L.sem3d_workspace_size.argtypes = [c_void_p, ctypes.POINTER(c_size_t)]
     L.sem3d_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
     L.sem3d_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
@@ -135,6 +137,11 @@ class Plan:
 
     def set_precision(self, precision: str = "fp64", sweeps: int = 1):
         _check(lib().sem3d_set_precision(self._h, PRECISIONS[precision], int(sweeps)), "sem3d_set_precision")
+
+    RESIDUALS = {"fp64": 0, "mixed": 1}
+
+    def set_residual(self, mode: str = "mixed"):
+        _check(lib().sem3d_set_residual(self._h, self.RESIDUALS[mode]), "sem3d_set_residual")
 
     def workspace_size(self) -> int:
         b = ctypes.c_size_t()

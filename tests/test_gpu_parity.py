@@ -108,6 +108,40 @@ def test_bf16x3_solve_matches_oracle(sem3d, i):
     assert _rel(refined, ref) < 1e-12
 
 
+@pytest.mark.parametrize("i", [2, 3, 5])
+@pytest.mark.parametrize("residual,sweeps", [("fp64", 3), ("mixed", 2), ("mixed", 4)])
+def test_bf16x3_residual_modes(sem3d, i, residual, sweeps):
+    # Mixed: double-FP32 residuals for all sweeps but the last, which is FP64.
+    n3, k, L3, c, (sx, sy, sz), F = _case(i)
+    ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.set_precision("bf16x3", sweeps)
+        p.set_residual(residual)
+        p.solve(f, u)
+        p.sync_check()
+        err = _rel(u.cpu().numpy(), ref)
+    # two sweeps reach ~1e-11 at most sizes: the bound is the contraction
+    # of two BF16x3 corrections; three or more reach rounding level.
+    assert err < (1e-12 if sweeps >= 3 else 1e-9), err
+
+
+def test_bf16x3_high_degree_falls_back_to_fp64_residuals(sem3d):
+    # k = 10 > 8: the double-FP32 stencil is not instantiated; every sweep is FP64.
+    n3, k, L3, c = (19, 29, 9), 10, (1.0, 1.0, 1.0), 1.0
+    sx, sy, sz = _axes(n3, k, L3)
+    F = random_rhs(*n3, seed=7)
+    ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.set_precision("bf16x3", 3)
+        p.solve(f, u)
+        p.sync_check()
+        assert _rel(u.cpu().numpy(), ref) < 1e-12
+
+
 def test_q2_n63_manufactured_both_paths(sem3d):
     # Q^2, Ne = 32 on [0,1]^3, n = 63, -Lap u = f, u = sin(pi x) sin(2 pi y) sin(3 pi z).
     s = sem_1d(2, 32, 0.0, 1.0)
