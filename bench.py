@@ -34,6 +34,24 @@ METRIC = "1000^3 Q^4 solve ms & GDoF/s on 1 GB300: FP64 vs refined split-BF16 at
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
+def tc_traffic_per_launch(n: int):
+    """DRAM bytes (read + write) of one tensor-core pass from the committed ncu
+    capture, scaled to n by the DoF processed; None once the kernel source has
+    changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_inputs.json")) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, ValueError, KeyError):
+        return None
+    if not sha.startswith(rec["source_sha256_prefix"]):
+        return None
+    px = (n + 15) // 16 * 16
+    return rec["dram_bytes_per_launch_n511"] * (px * n * n) / rec["dofs_per_launch_n511"]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -284,7 +302,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     achieved = flops_per_launch / (tc_avg_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
     roofline = {"kernel": "mode_product_bf16x3 (tcgen05)", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tc_traffic_per_launch(n),
+                "traffic_source": "profiles/roofline_inputs.json (ncu at n=511, scaled by DoF per launch)",
+                "algorithmic_bytes_per_launch": 8.0 * ((n + 15) // 16 * 16) * n * n,
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": tc_avg_ms, "launches": tc_n,
                 "share_of_step": tc_ms / (ms * args.steps)}

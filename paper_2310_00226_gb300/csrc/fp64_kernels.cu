@@ -294,7 +294,10 @@ cudaError_t launch_elem(const StencilArgs& a, const DevAxis* ax, int mode, cudaS
   const int nex = (a.nx + 1) / K;
   const long long total = (long long)nex * a.ny * a.nz;
   long long b = (total + 255) / 256;
-  if (b > 152LL * 64) b = 152LL * 64;
+  // One thread per work item (no grid-stride wrap): blocks are issued in
+  // order, so the resident set sweeps the grid plane by plane and the z
+  // neighbours of a plane are still in L2 when they are read again.
+  if (b > 0x7FFFFFFFLL) b = 0x7FFFFFFFLL;
   const int grid = (int)(b < 1 ? 1 : b);
   if (mode == 0) stencil_elem_kernel<K, 0><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
   else if (mode == 1) stencil_elem_kernel<K, 1><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
@@ -435,7 +438,7 @@ template <int K>
 cudaError_t launch_df(const DfArgs& a, cudaStream_t s) {
   const long long total = (long long)a.nex * a.ny * a.nz;
   long long b = (total + 255) / 256;
-  if (b > 152LL * 64) b = 152LL * 64;
+  if (b > 0x7FFFFFFFLL) b = 0x7FFFFFFFLL;  // one thread per work item (see launch_elem)
   stencil_df_kernel<K><<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -471,6 +474,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* in, __nv_bfloa
   }
 }
 
+// Grid of a streaming (grid-stride) kernel: enough blocks to fill the GPU a
+// few times over; each thread then walks the arrays in order.
 int grid_for(long long work, int per_block) {
   long long b = (work + per_block - 1) / per_block;
   if (b > 152LL * 32) b = 152LL * 32;
@@ -530,7 +535,7 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
     case 7: e = launch_elem<7>(a, ax, mode, s); break;
     case 8: e = launch_elem<8>(a, ax, mode, s); break;
     default:  // higher degrees: one thread per node, per-row band ranges
-      stencil_kernel<<<grid_for(N, 256), 256, 0, s>>>(a);
+      stencil_kernel<<<(int)((N + 255) / 256 < 0x7FFFFFFF ? (N + 255) / 256 : 0x7FFFFFFF), 256, 0, s>>>(a);
       e = cudaGetLastError();
   }
   if (e != cudaSuccess || mode != 2 || g.Px == g.nx) return e;

@@ -6,7 +6,8 @@ L-infinity against the oracle's refined FP64 solve):
   * FP64 mode products, no sweep                  : 1e-10 (bare solve, n*eps-level)
   * BF16x3 mode products, no sweep                : 5e-4 (about 16-bit operands,
     error amplified by the condition of the 1D bases; measured, not a target)
-  * BF16x3 + 3 FP64 sweeps                        : 1e-12
+  * BF16x3 + 3 sweeps (either residual mode)      : 1e-12
+  * BF16x3 + 2 sweeps                             : 1e-9 (two contractions of ~1e-4)
 The H-form operator apply is pure FP64 with a different summation order than
 the oracle's sparse products: 1e-13 relative to max |Au|.
 """
