@@ -54,12 +54,17 @@ typedef enum {
 
 /* Arithmetic of the six mode products of one solve (Section 2.4, Eq. 13).
  *   SEM3D_FP64   : FP64 operands and accumulation (mma.sync DMMA).
+ *   SEM3D_FP32   : FP32 operands and accumulation on the CUDA cores (FFMA).
+ *   SEM3D_BF16   : operands rounded to bfloat16, one product per element pair,
+ *                  FP32 accumulation on tcgen05 tensor cores (~8 bits).
  *   SEM3D_BF16X3 : operands split x = hi + lo into two bfloat16 numbers;
  *                  hi*hi + hi*lo + lo*hi accumulated in FP32 on tcgen05
  *                  tensor cores (about 16 significant bits per pass).
  * FP64 accuracy is recovered by iterative refinement (sem3d_set_precision). */
 typedef enum {
   SEM3D_FP64 = 0,
+  SEM3D_FP32 = 1,
+  SEM3D_BF16 = 4,
   SEM3D_BF16X3 = 5
 } sem3d_precision;
 
@@ -156,7 +161,8 @@ sem3d_status sem3d_sync_check(sem3d_handle h, void* stream);
  * 1 = FP64 (DMMA) mode product, 2 = FP64 stencil / residual, 3 = FP64 ->
  * split-bf16 conversion; the tensor-core launches of class 0 are also counted
  * by pass: 4 = x pass, 5 = y pass, 6 = z pass writing split-bf16 output,
- * 7 = the last pass of a solve (writes or accumulates FP64 u). */
+ * 7 = the last pass of a solve (writes or accumulates FP64 u); 8 = FP32
+ * CUDA-core mode product. */
 sem3d_status sem3d_profile(sem3d_handle h, int enable);
 sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms);
 

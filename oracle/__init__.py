@@ -27,4 +27,6 @@ from .sem import (  # noqa: F401
     refined_solve,
     dense_solve,
     l2_error_table1,
+    weak_matrix,
+    schrodinger_solve,
 )

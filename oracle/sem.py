@@ -301,3 +301,33 @@ def l2_error_table1(err: np.ndarray, Ne: int) -> float:
     The paper does not define it; this reading reproduces its printed values
     (see the Table 1 pin)."""
     return float(np.sqrt(np.sum(np.asarray(err) ** 2)) / Ne**1.5)
+
+
+# --------------------------------------------------------------------------
+# Schroedinger-type problem (Section 3.3, Eq. 15): alpha u - Lap u + V(x) u = f
+# --------------------------------------------------------------------------
+
+def weak_matrix(sx: Sem1D, sy: Sem1D, sz: Sem1D, diag_weight=None):
+    """Sparse weak-form matrix S(+)S(+)S + M3 diag(w) (Eq. 12 with the lumped
+    GLL quadrature of a variable zeroth-order coefficient w at the nodes;
+    x-fastest Kronecker order).  diag_weight: (nz, ny, nx) array or scalar."""
+    Sx, Sy, Sz = (sp.csr_matrix(s.S) for s in (sx, sy, sz))
+    Mx, My, Mz = (sp.diags(s.M) for s in (sx, sy, sz))
+    K = (sp.kron(Mz, sp.kron(My, Sx)) + sp.kron(Mz, sp.kron(Sy, Mx)) + sp.kron(Sz, sp.kron(My, Mx)))
+    if diag_weight is not None:
+        M3 = (sz.M[:, None, None] * sy.M[None, :, None] * sx.M[None, None, :]).reshape(-1)
+        w = np.broadcast_to(np.asarray(diag_weight, dtype=np.float64), (sz.n, sy.n, sx.n)).reshape(-1)
+        K = K + sp.diags(M3 * w)
+    return K.tocsc()
+
+
+def schrodinger_solve(F: np.ndarray, V: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Sem1D) -> np.ndarray:
+    """Plain definition of the discrete solution of -Lap u + V u = f (SEM with
+    lumped GLL quadrature, homogeneous Dirichlet data): solve
+    (S(+)S(+)S + M3 diag(V)) u = M3 f by a sparse direct factorisation.  The
+    paper solves it by PCG preconditioned with the fast solver of
+    (alpha + beta/2) - Lap (Section 3.3); the discrete solution is the same."""
+    import scipy.sparse.linalg as spla
+    K = weak_matrix(sx, sy, sz, V)
+    b = apply_mass(F, sx, sy, sz).reshape(-1)
+    return spla.spsolve(K, b).reshape(F.shape)

@@ -78,8 +78,8 @@ struct sem3d_plan {
   struct EvPair { int kind, sub, count; cudaEvent_t a, b; };
   std::vector<EvPair> pending;
   std::vector<cudaEvent_t> pool;
-  double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long prof_n[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -114,7 +114,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Kernel classes for sem3d_profile_read; tensor-core launches are also
 // counted per pass (x / y / z, and the last pass that writes FP64 u).
-enum { K_TC = 0, K_F64 = 1, K_STENCIL = 2, K_SPLIT = 3, K_TC_X = 4, K_TC_Y = 5, K_TC_Z = 6, K_TC_F64OUT = 7 };
+enum { K_TC = 0, K_F64 = 1, K_STENCIL = 2, K_SPLIT = 3, K_TC_X = 4, K_TC_Y = 5, K_TC_Z = 6, K_TC_F64OUT = 7, K_F32 = 8 };
 
 cudaEvent_t take_event(sem3d_plan* p) {
   if (!p->pool.empty()) {
@@ -158,11 +158,13 @@ struct LaunchScope {
 
 // Workspace layout per mode.
 //   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
-//   BF16X3 : two split arrays {hi, lo} of Px*ny*nz bf16 each, and the
+//   FP32   : two FP32 n^3 arrays (ping-pong) + one FP64 residual array.
+//   BF16X3 / BF16 : two split arrays {hi, lo} of Px*ny*nz bf16 each, and the
 //            double-FP32 solution (two FP32 n^3 arrays) used between sweeps.
 size_t workspace_bytes(const sem3d_plan* p) {
   const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
   if (p->prec == SEM3D_FP64) return 3 * align256(N * sizeof(double));
+  if (p->prec == SEM3D_FP32) return 2 * align256(N * sizeof(float)) + align256(N * sizeof(double));
   const size_t Ns = (size_t)p->g.Px * p->g.ny * p->g.nz;
   return 4 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(N * sizeof(float));
 }
@@ -199,27 +201,47 @@ sem3d_status solve_once_f64(sem3d_plan* p, const double* in, double* out, bool a
   return SEM3D_OK;
 }
 
+// ---- FP32 path: FP64 in -> FP64 out (store or accumulate), FP32 ping-pong.
+sem3d_status solve_once_f32(sem3d_plan* p, const double* in, double* out, bool accumulate, cudaStream_t s) {
+  const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
+  float* A = static_cast<float*>(p->ws);
+  float* B = reinterpret_cast<float*>(static_cast<char*>(p->ws) + align256(N * sizeof(float)));
+  const Geom& g = p->g;
+  const DevAxis* d = p->dev;
+  const double *lx = d[0].lam, *ly = d[1].lam, *lz = d[2].lam;
+  LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 2, d[2].Wf[0], in, true, A, false, EPI_STORE, lx, ly, lz, s));
+  LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 1, d[1].Wf[0], A, false, B, false, EPI_STORE, lx, ly, lz, s));
+  LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 0, d[0].Wf[0], B, false, A, false, EPI_DIV, lx, ly, lz, s));
+  LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 0, d[0].Wf[1], A, false, B, false, EPI_STORE, lx, ly, lz, s));
+  LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 1, d[1].Wf[1], B, false, A, false, EPI_STORE, lx, ly, lz, s));
+  LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 2, d[2].Wf[1], A, false, out, true,
+                                                 accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz, s));
+  return SEM3D_OK;
+}
+
 // ---- BF16x3 path: the split input is in buffer S0.  The last (z) pass
 // writes the result with epilogue `epi_last` into out64 and/or the
 // double-FP32 solution df.
 sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double* out64, int epi_last, DfBuffers df,
                                cudaStream_t s) {
+  const int np = (p->prec == SEM3D_BF16) ? 1 : 3;
+  const DfBuffers none{nullptr, nullptr};
   const Geom& g = p->g;
   const DevAxis* d = p->dev;
   const float *lx = d[0].lamf, *ly = d[1].lamf, *lz = d[2].lamf;
   const int sms = p->num_sms;
   int* e = p->d_err;
   // Forward: z, y, x with the division fused into the x pass (Eq. 13).
-  LAUNCH_SUB(p, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s, none, np));
   // Backward: x, y, z.  The mode products commute, so the order is free; the
   // z pass goes last because its TMEM lanes run along the contiguous index,
   // which makes the read-modify-write of the solution coalesced.
-  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
-  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s));
+  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
   LAUNCH_SUB(p, K_TC, K_TC_F64OUT, 1, s,
-             launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out64, epi_last, lx, ly, lz, e, sms, s, df));
+             launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out64, epi_last, lx, ly, lz, e, sms, s, df, np));
   return SEM3D_OK;
 }
 
@@ -283,6 +305,11 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
     }
     if ((st = dev_upload(p.get(), &D.band_lo, A.band_lo.data(), A.band_lo.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.band_hi, A.band_hi.data(), A.band_hi.size())) != SEM3D_OK) return st;
+    for (int w = 0; w < 2; ++w) {
+      const std::vector<double>& Wd = (w == 0) ? A.Tinv : A.T;
+      std::vector<float> wf(Wd.begin(), Wd.end());
+      if ((st = dev_upload(p.get(), &D.Wf[w], wf.data(), wf.size())) != SEM3D_OK) return st;
+    }
     std::vector<__nv_bfloat16> hi, lo;
     for (int w = 0; w < 2; ++w) {
       split_matrix(w == 0 ? A.Tinv : A.T, A.n, D.Kp, hi, lo);
@@ -303,13 +330,14 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
 
 sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweeps) {
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
-  if (prec != SEM3D_FP64 && prec != SEM3D_BF16X3) return fail(SEM3D_ERR_INVALID_ARG, "unknown precision");
+  if (prec != SEM3D_FP64 && prec != SEM3D_FP32 && prec != SEM3D_BF16 && prec != SEM3D_BF16X3)
+    return fail(SEM3D_ERR_INVALID_ARG, "unknown precision");
   if (sweeps < 0 || sweeps > 16) return fail(SEM3D_ERR_INVALID_ARG, "sweeps must be in [0, 16]");
-  if (prec == SEM3D_BF16X3) {
+  if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16) {
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
-    if (major != 10 || minor != 3) return fail(SEM3D_ERR_UNSUPPORTED, "BF16X3 needs an sm_103 GPU");
+    if (major != 10 || minor != 3) return fail(SEM3D_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 GPU");
   }
   h->prec = prec;
   h->sweeps = sweeps;
@@ -354,6 +382,13 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
       LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
       if ((st = solve_once_f64(h, r, u, true, s)) != SEM3D_OK) return st;
     }
+  } else if (h->prec == SEM3D_FP32) {
+    double* r = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(N * sizeof(float)));
+    if ((st = solve_once_f32(h, f, u, false, s)) != SEM3D_OK) return st;
+    for (int sw = 0; sw < h->sweeps; ++sw) {
+      LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+      if ((st = solve_once_f32(h, r, u, true, s)) != SEM3D_OK) return st;
+    }
   } else {
     const size_t Ns = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(__nv_bfloat16));
     const size_t Nf = align256(N * sizeof(float));
@@ -365,7 +400,7 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
     const int sw = h->sweeps;
     // Mixed residuals: sweeps 1 .. sw-1 in double-FP32 with the solution held
     // as a double-FP32 pair, the last sweep in FP64 on the FP64 solution.
-    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8;
+    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8 && h->prec == SEM3D_BF16X3;
     LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s));
     if (!mixed) {
       if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_STORE, none, s)) != SEM3D_OK) return st;
@@ -455,13 +490,13 @@ sem3d_status sem3d_profile(sem3d_handle h, int enable) {
     h->pool.push_back(ev.b);
   }
   h->pending.clear();
-  for (int q = 0; q < 8; ++q) { h->prof_ms[q] = 0.0; h->prof_n[q] = 0; }
+  for (int q = 0; q < 9; ++q) { h->prof_ms[q] = 0.0; h->prof_n[q] = 0; }
   h->profiling = enable != 0;
   return SEM3D_OK;
 }
 
 sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms) {
-  if (!h || kind < 0 || kind > 7) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
+  if (!h || kind < 0 || kind > 8) return fail(SEM3D_ERR_INVALID_ARG, "bad argument");
   for (auto& ev : h->pending) {
     CUDA_TRY(cudaEventSynchronize(ev.b));
     float ms = 0.f;

@@ -56,6 +56,7 @@ struct DevAxis {
   float* Hq_lo = nullptr;
   int* band_lo = nullptr;
   int* band_hi = nullptr;
+  float* Wf[2] = {nullptr, nullptr};            // FP32 copies: [0] = T^{-1}, [1] = T; n x n row-major
   __nv_bfloat16* W_hi[2] = {nullptr, nullptr};  // [0] = T^{-1}, [1] = T; n rows x Kp
   __nv_bfloat16* W_lo[2] = {nullptr, nullptr};
 };
@@ -89,6 +90,12 @@ struct Geom {
 cudaError_t launch_mode_product_f64(const Geom& g, int axis, const double* W, const double* in, double* out,
                                     int epi, const double* lamx, const double* lamy, const double* lamz,
                                     cudaStream_t s);
+// ---- FP32 CUDA-core kernels (fp32_kernels.cu)
+// One mode product in FP32 arithmetic; `in` is FP64 (first pass) or FP32,
+// `out` FP64 (last pass, EPI_STORE or EPI_ACCUM) or FP32.
+cudaError_t launch_mode_product_f32(const Geom& g, int axis, const float* W, const void* in, bool in_f64, void* out,
+                                    bool out_f64, int epi, const double* lamx, const double* lamy, const double* lamz,
+                                    cudaStream_t s);
 // Au = c u + (H_x (+) H_y (+) H_z) u            (mode 0)
 // r  = f - c u - (H_x (+) H_y (+) H_z) u        (mode 1, FP64 r)
 // r  = same, written as bf16 hi/lo at pitch Px   (mode 2)
@@ -116,6 +123,6 @@ struct TcPassPlan;
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
-                                       DfBuffers df = DfBuffers{nullptr, nullptr});
+                                       DfBuffers df = DfBuffers{nullptr, nullptr}, int nprod = 3);
 
 }  // namespace sem3d

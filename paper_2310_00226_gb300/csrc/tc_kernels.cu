@@ -257,7 +257,7 @@ __device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
 //   so each thread writes 16-byte vectors of its own line.
 // y / z passes: row = contiguous index (i, or i + Px*j), the output axis has
 //   a stride, and the 32 lanes of a warp write 32 consecutive elements.
-template <int PASS, int MODE>
+template <int PASS, int MODE, int NP>
 __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32]) {
   const bool full = col0 + 32 <= a.nout;
   if (PASS == 0) {
@@ -299,7 +299,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
         split_pair(v[8 * g + 4], v[8 * g + 5], hh.z, ll.z);
         split_pair(v[8 * g + 6], v[8 * g + 7], hh.w, ll.w);
         *reinterpret_cast<uint4*>(dh + 8 * g) = hh;
-        *reinterpret_cast<uint4*>(dl + 8 * g) = ll;
+        if (NP == 3) *reinterpret_cast<uint4*>(dl + 8 * g) = ll;
       }
     }
     return;
@@ -391,9 +391,9 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     for (int q = 0; q < 32; q += 2) {
       uint32_t hh, ll;
       split_pair(v[q], v[q + 1], hh, ll);
-      if (full || col0 + q < a.nout) { st_b16(ph, hh); st_b16(pl, ll); }
+      if (full || col0 + q < a.nout) { st_b16(ph, hh); if (NP == 3) st_b16(pl, ll); }
       ph += cs; pl += cs;
-      if (full || col0 + q + 1 < a.nout) { st_b16(ph, hh >> 16); st_b16(pl, ll >> 16); }
+      if (full || col0 + q + 1 < a.nout) { st_b16(ph, hh >> 16); if (NP == 3) st_b16(pl, ll >> 16); }
       ph += cs; pl += cs;
     }
   }
@@ -406,7 +406,9 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
 // BM = 128, BN = 256) by CL.  A stage may be refilled only when every CTA of
 // the cluster has finished the MMAs that read it: each CTA's MMA completion
 // arrives on the "empty" barrier of all CL CTAs (count CL).
-template <int PASS, int MODE, int CL>
+// NP = 3: BF16x3 (A_hi W_hi + A_hi W_lo + A_lo W_hi); NP = 1: single bf16
+// product A_hi W_hi (the lo arrays are neither loaded nor written).
+template <int PASS, int MODE, int CL, int NP>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -471,29 +473,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
         const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
-        mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+        mbar_arrive_expect_tx(full_bar(s), NP == 3 ? STAGE_BYTES : A_TILE_BYTES + B_TILE_BYTES);
         const int k0 = kb * BK;
         if (PASS == 0) {
           tma_load_2d(a_hi, &tmA_hi, full_bar(s), k0, m0);
-          tma_load_2d(a_lo, &tmA_lo, full_bar(s), k0, m0);
+          if (NP == 3) tma_load_2d(a_lo, &tmA_lo, full_bar(s), k0, m0);
         } else if (PASS == 1) {
           tma_load_3d(a_hi, &tmA_hi, full_bar(s), m0, k0, b);
           tma_load_3d(a_hi + A_TILE_BYTES / 2, &tmA_hi, full_bar(s), m0 + 64, k0, b);
-          tma_load_3d(a_lo, &tmA_lo, full_bar(s), m0, k0, b);
-          tma_load_3d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0, b);
+          if (NP == 3) {
+            tma_load_3d(a_lo, &tmA_lo, full_bar(s), m0, k0, b);
+            tma_load_3d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0, b);
+          }
         } else {
           tma_load_2d(a_hi, &tmA_hi, full_bar(s), m0, k0);
           tma_load_2d(a_hi + A_TILE_BYTES / 2, &tmA_hi, full_bar(s), m0 + 64, k0);
-          tma_load_2d(a_lo, &tmA_lo, full_bar(s), m0, k0);
-          tma_load_2d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0);
+          if (NP == 3) {
+            tma_load_2d(a_lo, &tmA_lo, full_bar(s), m0, k0);
+            tma_load_2d(a_lo + A_TILE_BYTES / 2, &tmA_lo, full_bar(s), m0 + 64, k0);
+          }
         }
         const uint32_t woff = (uint32_t)(rank * WROWS * BK * 2);
         if (CL == 1) {
           tma_load_2d(b_hi, &tmB_hi, full_bar(s), k0, n0);
-          tma_load_2d(b_lo, &tmB_lo, full_bar(s), k0, n0);
+          if (NP == 3) tma_load_2d(b_lo, &tmB_lo, full_bar(s), k0, n0);
         } else {
           tma_load_2d_mc(b_hi + woff, &tmB_hi, full_bar(s), k0, n0 + rank * WROWS, kMask);
-          tma_load_2d_mc(b_lo + woff, &tmB_lo, full_bar(s), k0, n0 + rank * WROWS, kMask);
+          if (NP == 3) tma_load_2d_mc(b_lo + woff, &tmB_lo, full_bar(s), k0, n0 + rank * WROWS, kMask);
         }
       }
     }
@@ -537,8 +543,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const uint64_t dbl = smem_desc(b_lo + k16 * 32u, 16u, 512u, LAYOUT_SW64);
           const uint32_t acc = (kb | k16) ? 1u : 0u;
           mma_bf16(tmem_d, dah, dbh, idesc, acc);
-          mma_bf16(tmem_d, dah, dbl, idesc, 1u);
-          mma_bf16(tmem_d, dal, dbh, idesc, 1u);
+          if (NP == 3) {
+            mma_bf16(tmem_d, dah, dbl, idesc, 1u);
+            mma_bf16(tmem_d, dal, dbh, idesc, 1u);
+          }
         }
         // The stage is free (in every CTA of the cluster) once these MMAs finish.
         if (CL == 1) mma_commit(empty_bar(s));
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
         float v[32];
         tmem_ld32(taddr + ch * 32, v);
-        epilogue_chunk<PASS, MODE>(a, row, col0, b, v);
+        epilogue_chunk<PASS, MODE, NP>(a, row, col0, b, v);
       }
       tc_fence_before();
       __syncwarp();
@@ -632,10 +640,10 @@ namespace {
 #endif
 constexpr int CLUSTER = SEM3D_TC_CLUSTER;
 
-template <int PASS, int MODE>
+template <int PASS, int MODE, int NP>
 cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                       const TcArgs& a, long long work_clusters, int num_sms, cudaStream_t s) {
-  auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER>;
+  auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER, NP>;
   static int max_clusters = 0;  // per instantiation: co-resident clusters of CLUSTER CTAs
   if (max_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -678,18 +686,27 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
 }
 
 template <int PASS>
-cudaError_t launch_tc_mode(int mode, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
+cudaError_t launch_tc_mode(int mode, int nprod, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
                            const CUtensorMap& b1, const TcArgs& a, long long work, int num_sms, cudaStream_t s) {
+  if (nprod == 1) {
+    switch (mode) {
+      case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      case OUT_F64: return launch_tc<PASS, OUT_F64, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      case OUT_F64_ACCUM: return launch_tc<PASS, OUT_F64_ACCUM, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (mode) {
-    case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT>(a0, a1, b0, b1, a, work, num_sms, s);
-    case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT>(a0, a1, b0, b1, a, work, num_sms, s);
-    case OUT_F64: return launch_tc<PASS, OUT_F64>(a0, a1, b0, b1, a, work, num_sms, s);
-    case OUT_F64_ACCUM: return launch_tc<PASS, OUT_F64_ACCUM>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT, 3>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT, 3>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_F64: return launch_tc<PASS, OUT_F64, 3>(a0, a1, b0, b1, a, work, num_sms, s);
+    case OUT_F64_ACCUM: return launch_tc<PASS, OUT_F64_ACCUM, 3>(a0, a1, b0, b1, a, work, num_sms, s);
     default:
       if constexpr (PASS == 2) {
-        if (mode == OUT_DF_STORE) return launch_tc<PASS, OUT_DF_STORE>(a0, a1, b0, b1, a, work, num_sms, s);
-        if (mode == OUT_DF_ACCUM) return launch_tc<PASS, OUT_DF_ACCUM>(a0, a1, b0, b1, a, work, num_sms, s);
-        return launch_tc<PASS, OUT_DF_ACCUM_F64>(a0, a1, b0, b1, a, work, num_sms, s);
+        if (mode == OUT_DF_STORE) return launch_tc<PASS, OUT_DF_STORE, 3>(a0, a1, b0, b1, a, work, num_sms, s);
+        if (mode == OUT_DF_ACCUM) return launch_tc<PASS, OUT_DF_ACCUM, 3>(a0, a1, b0, b1, a, work, num_sms, s);
+        return launch_tc<PASS, OUT_DF_ACCUM_F64, 3>(a0, a1, b0, b1, a, work, num_sms, s);
       }
       return cudaErrorInvalidValue;
   }
@@ -705,7 +722,8 @@ static constexpr CUtensorMapSwizzle SWZ_MN = CU_TENSOR_MAP_SWIZZLE_128B;
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
-                                       DfBuffers df) {
+                                       DfBuffers df, int nprod) {
+  if (nprod != 1 && nprod != 3) return cudaErrorInvalidValue;
   int mode;
   if (epi == EPI_DF_STORE || epi == EPI_DF_ACCUM || epi == EPI_DF_ACCUM_F64) {
     if (axis != 2 || !df.hi || !df.lo || (epi == EPI_DF_ACCUM_F64 && !out64)) return cudaErrorInvalidValue;
@@ -764,9 +782,9 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   a.k_blocks = (nin + BK - 1) / BK;
   const long long work = (long long)((a.m_tiles + CLUSTER - 1) / CLUSTER) * a.n_tiles * a.batches;
   if (work >= (1LL << 31)) return cudaErrorInvalidValue;
-  if (axis == 0) return launch_tc_mode<0>(mode, mAh, mAl, mBh, mBl, a, work, num_sms, s);
-  if (axis == 1) return launch_tc_mode<1>(mode, mAh, mAl, mBh, mBl, a, work, num_sms, s);
-  return launch_tc_mode<2>(mode, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  if (axis == 0) return launch_tc_mode<0>(mode, nprod, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  if (axis == 1) return launch_tc_mode<1>(mode, nprod, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  return launch_tc_mode<2>(mode, nprod, mAh, mAl, mBh, mBl, a, work, num_sms, s);
 }
 
 }  // namespace sem3d

@@ -117,3 +117,19 @@ def table1_neumann(x, y, z, alpha: float = 1.0):
     f = ((alpha + 14 * PI**2) * s + alpha * _outer3(p, q, r)
          - (_outer3(pdd, q, r) + _outer3(p, qdd, r) + _outer3(p, q, rdd)))
     return u, f
+
+
+def harmonic_potential(x, y, z, amp: float = 100.0):
+    """V(x) = amp |x - (0.5, 0.5, 0.5)|^2 at the nodes (the Schroedinger PCG
+    workload on [0,1]^3); its mean over the unit cube is amp / 4."""
+    x, y, z = (np.asarray(t) for t in (x, y, z))
+    return amp * ((np.asarray(z)[:, None, None] - 0.5) ** 2 + (np.asarray(y)[None, :, None] - 0.5) ** 2
+                  + (np.asarray(x)[None, None, :] - 0.5) ** 2)
+
+
+def schrodinger_manufactured(x, y, z, amp: float = 100.0):
+    """(u, V, f) with u = sin(pi x) sin(pi y) sin(pi z) and V = harmonic_potential:
+    f = -Lap u + V u = (3 pi^2 + V) u."""
+    u = _outer3(np.sin(PI * np.asarray(x)), np.sin(PI * np.asarray(y)), np.sin(PI * np.asarray(z)))
+    V = harmonic_potential(x, y, z, amp)
+    return u, V, (3 * PI**2 + V) * u

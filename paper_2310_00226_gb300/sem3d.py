@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsem3d.s
 
 SEM3D_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "UNSUPPORTED"}
-PRECISIONS = {"fp64": 0, "bf16x3": 5}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 4, "bf16x3": 5}
 
 #: Every entry point declared in include/sem3d.h.
 EXPORTS = (
@@ -166,7 +166,7 @@ class Plan:
         _check(lib().sem3d_sync_check(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_sync_check")
 
     KERNEL_CLASSES = {"tc_mode_product": 0, "f64_mode_product": 1, "stencil": 2, "split": 3,
-                      "tc_x": 4, "tc_y": 5, "tc_z": 6, "tc_f64_out": 7}
+                      "tc_x": 4, "tc_y": 5, "tc_z": 6, "tc_f64_out": 7, "f32_mode_product": 8}
 
     def profile(self, enable: bool = True):
         _check(lib().sem3d_profile(self._h, 1 if enable else 0), "sem3d_profile")

@@ -259,3 +259,42 @@ def test_pins_catch_planted_mistakes(what):
     # and a dropped shift term
     bad_c = fast_solve(F, sx, sy, sz, 0.0)
     assert np.abs(bad_c - u_ref).max() / np.abs(u_ref).max() > 1e-3
+
+
+# ---------------------------------------------------------------- Schroedinger oracle
+
+def test_schrodinger_constant_potential_reduces_to_fast_solve():
+    # V = c0 everywhere: -Lap u + c0 u = f is the shifted Poisson problem whose
+    # fast solve is pinned above (dense LU, Table 1).
+    from oracle import schrodinger_solve
+    sx, sy, sz = sem_1d(2, 4, 0.0, 1.0), sem_1d(3, 3, 0.0, 0.8), sem_1d(2, 5, 0.0, 1.1)
+    F = random_rhs(sx.n, sy.n, sz.n, seed=12)
+    V = np.full(F.shape, 2.5)
+    u = schrodinger_solve(F, V, sx, sy, sz)
+    ref = fast_solve(F, sx, sy, sz, 2.5)
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-12
+
+
+def test_schrodinger_manufactured_convergence_order():
+    # Variable V: nodal error decreases at order k+2 (Section 3.1's rate for the
+    # SEM with lumped quadrature).
+    from oracle import schrodinger_solve
+    from paper_2310_00226_gb300.inputs import schrodinger_manufactured
+    errs = []
+    for Ne in (4, 8):
+        s = sem_1d(2, Ne, 0.0, 1.0)
+        u, V, F = schrodinger_manufactured(s.x, s.x, s.x)
+        uh = schrodinger_solve(F, V, s, s, s)
+        errs.append(np.sqrt(np.mean((uh - u) ** 2)))
+    order = math.log2(errs[0] / errs[1])
+    assert abs(order - 4) < 0.5, order
+
+
+def test_harmonic_potential_mean():
+    # mean of 100 |x - 1/2|^2 over [0,1]^3 = 100 * 3/12 = 25; GLL quadrature on
+    # all nodes (boundary included) integrates this quadratic exactly.
+    from paper_2310_00226_gb300.inputs import harmonic_potential
+    s = sem_1d(4, 16, 0.0, 1.0, bc="neumann")
+    V = harmonic_potential(s.x, s.x, s.x)
+    w = s.M[:, None, None] * s.M[None, :, None] * s.M[None, None, :]
+    assert abs((V * w).sum() / w.sum() - 25.0) < 1e-12
