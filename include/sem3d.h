@@ -126,6 +126,29 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
  * in FP64.  u, Au: device FP64 arrays, must not overlap. */
 sem3d_status sem3d_apply(sem3d_handle h, const double* u, double* Au, void* stream);
 
+/* Preconditioned conjugate gradient for -Lap u + V(x) u = f (Section 3.3,
+ * Eq. 15: the SEM operator with a variable potential, preconditioned by the
+ * fast solver of a constant-coefficient operator; the paper uses
+ * (alpha + beta/2) - Lap).  The preconditioner is this plan's solve: its shift
+ * c (sem3d_setup) is the constant (e.g. the mean of V), its precision and
+ * sweeps (sem3d_set_precision) its arithmetic.  Operator apply (banded FP64
+ * stencil plus V u), dot products and vector updates are FP64.  The inner
+ * product is weighted by the lumped GLL mass M (x) M (x) M, which makes the
+ * iteration CG on the symmetric weak form S(+)S(+)S + (M(x)M(x)M) diag(V).
+ *   V, f   : device FP64 nodal arrays (layout as in sem3d_solve).
+ *   u      : device FP64 solution, overwritten; the iteration starts at u = 0.
+ *   rtol   : stop when ||M3 r||_2 <= rtol * ||M3 f||_2 (weak-form residual).
+ *   maxit  : iteration limit, >= 1.
+ *   iters, relres : host outputs (may be NULL): iterations run, final ratio.
+ * Every iteration after the first replays a CUDA graph of the iteration body
+ * on a plan-owned stream joined to `stream` by events; the host reads the
+ * residual norm after each iteration, so the call is synchronous.  Uses six
+ * FP64 arrays of nx*ny*nz plan-owned device memory (allocated on first use).
+ * Returns SEM3D_ERR_NOT_CONVERGED when maxit is reached or the residual
+ * becomes non-finite (iters and relres are still written). */
+sem3d_status sem3d_pcg(sem3d_handle h, const double* V, const double* f, double* u, double rtol, int maxit,
+                       int* iters, double* relres, void* stream);
+
 /* Axis data (axis 0 = x, 1 = y, 2 = z), copied to host memory; synchronous.
  *   x_host      : n_axis node coordinates of the interior nodes.
  *   lambda_host : n_axis eigenvalues of H, ascending (may be NULL).

@@ -78,6 +78,10 @@ struct sem3d_plan {
   struct EvPair { int kind, sub, count; cudaEvent_t a, b; };
   std::vector<EvPair> pending;
   std::vector<cudaEvent_t> pool;
+  // PCG: six FP64 n^3 vectors, scalars, an internal stream (allocated on first use)
+  double* pcg_buf = nullptr;
+  PcgScalars* pcg_sc = nullptr;
+  cudaStream_t pcg_stream = nullptr;
   double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   long long prof_n[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
@@ -245,6 +249,8 @@ sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double
   return SEM3D_OK;
 }
 
+sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s);
+
 }  // namespace
 
 extern "C" {
@@ -284,6 +290,7 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
     DevAxis& D = p->dev[a];
     D.n = A.n; D.k = k; D.Kp = pad16(A.n);
     sem3d_status st;
+    if ((st = dev_upload(p.get(), &D.M, A.M.data(), A.M.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.T, A.T.data(), A.T.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.Tinv, A.Tinv.data(), A.Tinv.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.lam, A.lam.data(), A.lam.size())) != SEM3D_OK) return st;
@@ -372,9 +379,19 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
   if (!h || !f || !u) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
   const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
   if (f == u || (f < u + N && u < f + N)) return fail(SEM3D_ERR_INVALID_ARG, "f and u overlap");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   sem3d_status st = ensure_workspace(h);
   if (st != SEM3D_OK) return st;
+  return run_solve(h, f, u, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace {
+
+// The solve itself (arguments already checked, workspace present).
+sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s) {
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  sem3d_status st = SEM3D_OK;
   if (h->prec == SEM3D_FP64) {
     double* r = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(N * sizeof(double)));
     if ((st = solve_once_f64(h, f, u, false, s)) != SEM3D_OK) return st;
@@ -423,6 +440,10 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
   }
   return SEM3D_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 sem3d_status sem3d_apply(sem3d_handle h, const double* u, double* Au, void* stream) {
   if (!h || !u || !Au) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
@@ -522,9 +543,114 @@ sem3d_status sem3d_launch_count(sem3d_handle h, unsigned long long* count) {
   return SEM3D_OK;
 }
 
+sem3d_status sem3d_pcg(sem3d_handle h, const double* V, const double* f, double* u, double rtol, int maxit,
+                       int* iters, double* relres, void* stream) {
+  if (!h || !V || !f || !u) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(rtol > 0.0) || maxit < 1) return fail(SEM3D_ERR_INVALID_ARG, "need rtol > 0 and maxit >= 1");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  if (u < f + N && f < u + N) return fail(SEM3D_ERR_INVALID_ARG, "f and u overlap");
+  if (u < V + N && V < u + N) return fail(SEM3D_ERR_INVALID_ARG, "V and u overlap");
+  sem3d_status st = ensure_workspace(h);
+  if (st != SEM3D_OK) return st;
+  if (!h->pcg_buf) {
+    void* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, 6 * align256(N * sizeof(double))));
+    h->pcg_buf = static_cast<double*>(d);
+    CUDA_TRY(cudaMalloc(&d, sizeof(PcgScalars)));
+    h->pcg_sc = static_cast<PcgScalars*>(d);
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->pcg_stream, cudaStreamNonBlocking));
+  }
+  const size_t stride = align256(N * sizeof(double)) / sizeof(double);
+  PcgArgs a{};
+  a.N = (long long)N;
+  a.nx = h->g.nx; a.ny = h->g.ny; a.nz = h->g.nz;
+  a.Mx = h->dev[0].M; a.My = h->dev[1].M; a.Mz = h->dev[2].M;
+  a.c = h->g.c;
+  a.V = V; a.f = f; a.u = u;
+  a.r = h->pcg_buf; a.z = a.r + stride; a.p = a.z + stride; a.q = a.p + stride; a.M3 = a.q + stride;
+  a.Vmc = a.M3 + stride;
+  a.sc = h->pcg_sc;
+  // The iteration runs on the plan's own stream, joined to the caller's
+  // stream by events at both ends (the caller's stream may be the legacy
+  // default stream, which cannot be captured into a graph).
+  cudaStream_t cs = static_cast<cudaStream_t>(stream), s = h->pcg_stream;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  CUDA_TRY(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } guard{ev0, ev1};
+  CUDA_TRY(cudaEventRecord(ev0, cs));
+  CUDA_TRY(cudaStreamWaitEvent(s, ev0, 0));
+  CUDA_TRY(cudaMemsetAsync(a.sc, 0, sizeof(PcgScalars), s));
+  LAUNCH(h, K_STENCIL, 1, s, launch_pcg(PCG_INIT, a, s));
+  // One iteration: z = P r, beta, p = z + beta p, q = A_V p, alpha, u and r.
+  auto body = [&](cudaStream_t bs) -> sem3d_status {
+    sem3d_status bst = run_solve(h, a.r, a.z, bs);
+    if (bst != SEM3D_OK) return bst;
+    LAUNCH(h, K_STENCIL, 1, bs, launch_pcg(PCG_DOT_RZ, a, bs));
+    LAUNCH(h, K_STENCIL, 1, bs, launch_pcg(PCG_BETA, a, bs));
+    LAUNCH(h, K_STENCIL, 1, bs, launch_pcg(PCG_P, a, bs));
+    LAUNCH(h, K_STENCIL, 1, bs, launch_stencil(h->g, h->k, h->dev, a.p, nullptr, a.q, nullptr, nullptr, 0, bs));
+    LAUNCH(h, K_STENCIL, 1, bs, launch_pcg(PCG_Q, a, bs));
+    LAUNCH(h, K_STENCIL, 1, bs, launch_pcg(PCG_UPDATE, a, bs));
+    LAUNCH(h, K_STENCIL, 1, bs, launch_pcg(PCG_COUNT, a, bs));
+    return SEM3D_OK;
+  };
+  PcgScalars host{};
+  auto read = [&]() -> sem3d_status {
+    CUDA_TRY(cudaMemcpyAsync(&host, a.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SEM3D_OK;
+  };
+  // First iteration runs eagerly (it also performs one-time launch set-up),
+  // the rest replay a captured graph of the same body.
+  if ((st = body(s)) != SEM3D_OK) return st;
+  if ((st = read()) != SEM3D_OK) return st;
+  double rr = host.bnorm2 > 0.0 ? std::sqrt(host.rnorm2 / host.bnorm2) : 0.0;
+  int it = 1;
+  cudaGraphExec_t exec = nullptr;
+  if (rr > rtol && std::isfinite(rr) && it < maxit) {
+    const bool prof = h->profiling;
+    h->profiling = false;  // no event records inside the captured body
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    st = body(s);
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    h->profiling = prof;
+    if (st != SEM3D_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture(pcg)");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate(pcg)");
+  }
+  struct ExecGuard {
+    cudaGraphExec_t e;
+    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+  } eg{exec};
+  while (rr > rtol && std::isfinite(rr) && it < maxit) {
+    CUDA_TRY(cudaGraphLaunch(exec, s));
+    // kernels in the graph: one solve + 7 PCG launches
+    if ((st = read()) != SEM3D_OK) return st;
+    rr = host.bnorm2 > 0.0 ? std::sqrt(host.rnorm2 / host.bnorm2) : 0.0;
+    ++it;
+  }
+  CUDA_TRY(cudaEventRecord(ev1, s));
+  CUDA_TRY(cudaStreamWaitEvent(cs, ev1, 0));
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  if (!std::isfinite(rr)) return fail(SEM3D_ERR_NOT_CONVERGED, "PCG residual is not finite");
+  if (rr > rtol) return fail(SEM3D_ERR_NOT_CONVERGED, "PCG reached maxit before rtol");
+  return SEM3D_OK;
+}
+
 sem3d_status sem3d_destroy(sem3d_handle h) {
   if (!h) return SEM3D_OK;
   cudaError_t e = cudaDeviceSynchronize();
+  if (h->pcg_buf) cudaFree(h->pcg_buf);
+  if (h->pcg_sc) cudaFree(h->pcg_sc);
+  if (h->pcg_stream) cudaStreamDestroy(h->pcg_stream);
   for (auto& ev : h->pending) { h->pool.push_back(ev.a); h->pool.push_back(ev.b); }
   for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
   if (h->ws && h->ws_owned) cudaFree(h->ws);

@@ -46,6 +46,7 @@ inline int pad16(int n) { return (n + 15) & ~15; }
 
 struct DevAxis {
   int n = 0, k = 0, Kp = 0;     // Kp = pad16(n): row pitch of the bf16 matrices
+  double* M = nullptr;          // FP64 lumped mass diagonal (n)
   double* T = nullptr;          // FP64 n x n row-major (W[out][in] for the backward pass)
   double* Tinv = nullptr;       // FP64 n x n row-major (W[out][in] for the forward pass)
   double* lam = nullptr;        // FP64 eigenvalues
@@ -124,5 +125,23 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
                                        DfBuffers df = DfBuffers{nullptr, nullptr}, int nprod = 3);
+
+// ---- PCG vector kernels (pcg_kernels.cu)
+struct PcgScalars {
+  double rz_old, rz_new, pq, beta, rnorm2, bnorm2;
+  long long iter;
+};
+struct PcgArgs {
+  long long N;
+  int nx, ny, nz;
+  const double *Mx, *My, *Mz;
+  double c;                 // shift of the preconditioner (inside the stencil's H table)
+  const double* V;
+  const double* f;
+  double *u, *r, *z, *p, *q, *M3, *Vmc;
+  PcgScalars* sc;
+};
+enum { PCG_INIT = 0, PCG_DOT_RZ, PCG_BETA, PCG_P, PCG_Q, PCG_UPDATE, PCG_COUNT };
+cudaError_t launch_pcg(int op, const PcgArgs& a, cudaStream_t s);
 
 }  // namespace sem3d

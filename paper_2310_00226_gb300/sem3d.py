@@ -31,6 +31,7 @@ EXPORTS = (
     "sem3d_set_workspace",
     "sem3d_solve",
     "sem3d_apply",
+    "sem3d_pcg",
     "sem3d_get_nodes",
     "sem3d_get_eigs",
     "sem3d_axis_info",
@@ -69,6 +70,8 @@ def lib() -> ctypes.CDLL:
     L.sem3d_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
     L.sem3d_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_pcg.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.POINTER(c_int),
+                            ctypes.POINTER(c_double), c_void_p]
     L.sem3d_get_nodes.argtypes = [c_void_p, c_int, c_void_p]
     L.sem3d_get_eigs.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
     L.sem3d_axis_info.argtypes = [c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
@@ -161,6 +164,17 @@ class Plan:
         _check(lib().sem3d_apply(self._h, ctypes.c_void_p(_dev_ptr(u, self.numel, "u")),
                                  ctypes.c_void_p(_dev_ptr(Au, self.numel, "Au")), ctypes.c_void_p(_stream_ptr(stream))),
                "sem3d_apply")
+
+    def pcg(self, V, f, u, rtol: float = 1e-10, maxit: int = 200, stream=None, check: bool = True):
+        """PCG for -Lap u + V u = f preconditioned by this plan's solve; returns (iters, relres)."""
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = lib().sem3d_pcg(self._h, ctypes.c_void_p(_dev_ptr(V, self.numel, "V")),
+                             ctypes.c_void_p(_dev_ptr(f, self.numel, "f")), ctypes.c_void_p(_dev_ptr(u, self.numel, "u")),
+                             float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rr),
+                             ctypes.c_void_p(_stream_ptr(stream)))
+        if check:
+            _check(st, "sem3d_pcg")
+        return it.value, rr.value
 
     def sync_check(self, stream=None):
         _check(lib().sem3d_sync_check(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_sync_check")
