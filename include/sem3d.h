@@ -149,6 +149,34 @@ sem3d_status sem3d_apply(sem3d_handle h, const double* u, double* Au, void* stre
 sem3d_status sem3d_pcg(sem3d_handle h, const double* V, const double* f, double* u, double rtol, int maxit,
                        int* iters, double* relres, void* stream);
 
+/* One BDF2 time step of the Cahn-Hilliard equation (Section 3.5, Eqs. 17-20):
+ * phi_t = m Lap mu, mu = -eps Lap phi + F'(phi)/eps, F(phi) = (phi^2-1)^2/4,
+ * with homogeneous Dirichlet data for phi and Lap phi.  With a = 3/2,
+ * phi_hat = 2 phi_n - phi_{n-1}/2, phi_bar = 2 phi_n - phi_{n-1}:
+ *   (a + dt m (eps Lap^2 - (S/eps) Lap)) phi_{n+1}
+ *        = phi_hat + (dt m / eps) Lap (F'(phi_bar) - S phi_bar),
+ * solved in the plan's eigenbasis (the paper's Eq. 20: the two operators
+ * share T): prep, two forward transforms, a pointwise combination, one
+ * backward transform (9 mode products).  S is a stabilisation constant (the
+ * paper borrows one without printing it; this reading adds
+ * (S/eps)(phi_{n+1} - phi_bar) to mu; S = 0 is the printed scheme).
+ * Arithmetic: the plan's precision (FP64 DMMA, FP32, BF16X3 or BF16 tensor
+ * cores; no refinement), the plan's shift c is not used.
+ *   phi_n, phi_nm1 : device FP64 arrays (layout as in sem3d_solve).
+ *   phi_np1        : device FP64 output, must not overlap the inputs.
+ *   eps, m, dt > 0, S >= 0. */
+sem3d_status sem3d_ch_step(sem3d_handle h, const double* phi_n, const double* phi_nm1, double* phi_np1, double eps,
+                           double m, double dt, double S, void* stream);
+
+/* nsteps BDF2 steps in place: on entry phi_nm1, phi_n hold phi_{-1}, phi_0
+ * (pass the same values twice for a cold start), on return phi_{N-1}, phi_N.
+ * Steps run on a plan-owned stream joined to `stream` by events; after the
+ * first step, groups of three steps are replayed from one CUDA graph (three
+ * steps rotate the three phi buffers back to their roles).  Uses one extra
+ * plan-owned FP64 array (allocated on first use).  Asynchronous. */
+sem3d_status sem3d_ch_run(sem3d_handle h, double* phi_nm1, double* phi_n, int nsteps, double eps, double m, double dt,
+                          double S, void* stream);
+
 /* Axis data (axis 0 = x, 1 = y, 2 = z), copied to host memory; synchronous.
  *   x_host      : n_axis node coordinates of the interior nodes.
  *   lambda_host : n_axis eigenvalues of H, ascending (may be NULL).

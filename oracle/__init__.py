@@ -29,4 +29,6 @@ from .sem import (  # noqa: F401
     l2_error_table1,
     weak_matrix,
     schrodinger_solve,
+    assembled_h3,
+    ch_step,
 )

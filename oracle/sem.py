@@ -331,3 +331,38 @@ def schrodinger_solve(F: np.ndarray, V: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Se
     K = weak_matrix(sx, sy, sz, V)
     b = apply_mass(F, sx, sy, sz).reshape(-1)
     return spla.spsolve(K, b).reshape(F.shape)
+
+
+# --------------------------------------------------------------------------
+# Cahn-Hilliard BDF2 step (Section 3.5, Eqs. 17-20)
+# --------------------------------------------------------------------------
+
+def assembled_h3(sx: Sem1D, sy: Sem1D, sz: Sem1D) -> np.ndarray:
+    """Dense H3 = I(x)I(x)H_x + I(x)H_y(x)I + H_z(x)I(x)I (x fastest): the
+    discrete -Lap in H form (Eq. 12)."""
+    Ix, Iy, Iz = (np.eye(s.n) for s in (sx, sy, sz))
+    return np.kron(Iz, np.kron(Iy, sx.H)) + np.kron(Iz, np.kron(sy.H, Ix)) + np.kron(sz.H, np.kron(Iy, Ix))
+
+
+def ch_step(phi_n: np.ndarray, phi_nm1: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Sem1D,
+            eps: float, m: float, dt: float, S: float = 0.0) -> np.ndarray:
+    """One BDF2 step of the Cahn-Hilliard system (Eq. 19, with the chemical
+    potential eliminated as in Eq. 20), on small grids, by a dense solve.
+
+    phi_t = m Lap mu, mu = -eps Lap phi + F'(phi)/eps, F'(phi) = phi^3 - phi;
+    BDF2 with a = 3/2, phi_hat = 2 phi_n - phi_{n-1}/2, extrapolated
+    phi_bar = 2 phi_n - phi_{n-1} in the nonlinear term.  The stabilisation
+    the paper borrows (Section 3.5.2, formula not printed) is read as
+    mu_{n+1} += (S/eps)(phi_{n+1} - phi_bar); S = 0 is the paper's scheme.
+    With -Lap -> H3 (homogeneous Dirichlet data for phi and Lap phi):
+      (a + dt m (eps H3^2 + (S/eps) H3)) phi_{n+1}
+          = phi_hat - dt m H3 g,   g = (F'(phi_bar) - S phi_bar) / eps.
+    """
+    H3 = assembled_h3(sx, sy, sz)
+    a = 1.5
+    phi_hat = 2.0 * phi_n - 0.5 * phi_nm1
+    phi_bar = 2.0 * phi_n - phi_nm1
+    g = (phi_bar**3 - phi_bar - S * phi_bar) / eps
+    P = a * np.eye(H3.shape[0]) + dt * m * (eps * H3 @ H3 + (S / eps) * H3)
+    rhs = phi_hat.reshape(-1) - dt * m * (H3 @ g.reshape(-1))
+    return np.linalg.solve(P, rhs).reshape(phi_n.shape)

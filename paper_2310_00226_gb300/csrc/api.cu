@@ -81,6 +81,7 @@ struct sem3d_plan {
   // PCG: six FP64 n^3 vectors, scalars, an internal stream (allocated on first use)
   double* pcg_buf = nullptr;
   PcgScalars* pcg_sc = nullptr;
+  double* ch_buf = nullptr;  // third phi buffer of sem3d_ch_run
   cudaStream_t pcg_stream = nullptr;
   double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   long long prof_n[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -163,14 +164,15 @@ struct LaunchScope {
 // Workspace layout per mode.
 //   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
 //   FP32   : two FP32 n^3 arrays (ping-pong) + one FP64 residual array.
-//   BF16X3 / BF16 : two split arrays {hi, lo} of Px*ny*nz bf16 each, and the
-//            double-FP32 solution (two FP32 n^3 arrays) used between sweeps.
+//   BF16X3 / BF16 : three split arrays {hi, lo} of Px*ny*nz bf16 each (the
+//            third serves the Cahn-Hilliard step), and the double-FP32
+//            solution (two FP32 n^3 arrays) used between sweeps.
 size_t workspace_bytes(const sem3d_plan* p) {
   const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
   if (p->prec == SEM3D_FP64) return 3 * align256(N * sizeof(double));
   if (p->prec == SEM3D_FP32) return 2 * align256(N * sizeof(float)) + align256(N * sizeof(double));
   const size_t Ns = (size_t)p->g.Px * p->g.ny * p->g.nz;
-  return 4 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(N * sizeof(float));
+  return 6 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(N * sizeof(float));
 }
 
 sem3d_status ensure_workspace(sem3d_plan* p) {
@@ -412,7 +414,7 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
     char* w = static_cast<char*>(h->ws);
     TcBuffers S0{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
     TcBuffers S1{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
-    DfBuffers D{reinterpret_cast<float*>(w + 4 * Ns), reinterpret_cast<float*>(w + 4 * Ns + Nf)};
+    DfBuffers D{reinterpret_cast<float*>(w + 6 * Ns), reinterpret_cast<float*>(w + 6 * Ns + Nf)};
     const DfBuffers none{nullptr, nullptr};
     const int sw = h->sweeps;
     // Mixed residuals: sweeps 1 .. sw-1 in double-FP32 with the solution held
@@ -645,8 +647,176 @@ sem3d_status sem3d_pcg(sem3d_handle h, const double* V, const double* f, double*
   return SEM3D_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One Cahn-Hilliard BDF2 step in the plan's arithmetic tier (see
+// csrc/ch_kernels.cu for the formula): prep, two forward transforms (z, y, x
+// with T^{-1}), pointwise combination in the eigenbasis, backward transform
+// (x, y, z with T) writing FP64 phi_{n+1}.
+sem3d_status ch_step_core(sem3d_plan* h, const double* phi_n, const double* phi_nm1, double* phi_np1,
+                          const ChParams& c, cudaStream_t s) {
+  const Geom& g = h->g;
+  const DevAxis* d = h->dev;
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  char* w = static_cast<char*>(h->ws);
+  const TcBuffers nb{nullptr, nullptr};
+  if (h->prec == SEM3D_FP64) {
+    double* A = reinterpret_cast<double*>(w);
+    double* B = reinterpret_cast<double*>(w + align256(N * sizeof(double)));
+    double* R = reinterpret_cast<double*>(w + 2 * align256(N * sizeof(double)));
+    LAUNCH(h, K_STENCIL, 1, s, launch_ch_prep(SEM3D_FP64, g, phi_n, phi_nm1, A, B, nb, nb, c, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].Tinv, A, R, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].Tinv, R, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].Tinv, A, R, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].Tinv, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_STENCIL, 1, s, launch_ch_combine(SEM3D_FP64, g, d, R, A, B, nb, nb, nb, c, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].T, A, R, EPI_STORE, nullptr, nullptr, nullptr, s));
+    LAUNCH(h, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].T, R, phi_np1, EPI_STORE, nullptr, nullptr, nullptr, s));
+  } else if (h->prec == SEM3D_FP32) {
+    float* A = reinterpret_cast<float*>(w);
+    float* B = reinterpret_cast<float*>(w + align256(N * sizeof(float)));
+    float* C = reinterpret_cast<float*>(w + 2 * align256(N * sizeof(float)));
+    const double *lx = d[0].lam, *ly = d[1].lam, *lz = d[2].lam;
+    LAUNCH(h, K_STENCIL, 1, s, launch_ch_prep(SEM3D_FP32, g, phi_n, phi_nm1, A, B, nb, nb, c, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 2, d[2].Wf[0], A, false, C, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 1, d[1].Wf[0], C, false, A, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 0, d[0].Wf[0], A, false, C, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 2, d[2].Wf[0], B, false, A, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 1, d[1].Wf[0], A, false, B, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 0, d[0].Wf[0], B, false, A, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_STENCIL, 1, s, launch_ch_combine(SEM3D_FP32, g, d, C, A, B, nb, nb, nb, c, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 0, d[0].Wf[1], B, false, A, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 1, d[1].Wf[1], A, false, C, false, EPI_STORE, lx, ly, lz, s));
+    LAUNCH(h, K_F32, 1, s, launch_mode_product_f32(g, 2, d[2].Wf[1], C, false, phi_np1, true, EPI_STORE, lx, ly, lz, s));
+  } else {
+    const size_t Ns = align256((size_t)g.Px * g.ny * g.nz * sizeof(__nv_bfloat16));
+    TcBuffers S0{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
+    TcBuffers S1{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
+    TcBuffers S2{reinterpret_cast<__nv_bfloat16*>(w + 4 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 5 * Ns)};
+    const float *lx = d[0].lamf, *ly = d[1].lamf, *lz = d[2].lamf;
+    const int sms = h->num_sms, np = (h->prec == SEM3D_BF16) ? 1 : 3;
+    int* e = h->d_err;
+    const DfBuffers none{nullptr, nullptr};
+    LAUNCH(h, K_SPLIT, 1, s, launch_ch_prep(SEM3D_BF16X3, g, phi_n, phi_nm1, nullptr, nullptr, S0, S2, c, s));
+    LAUNCH_SUB(h, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S2, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S0, S2, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S2, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH(h, K_SPLIT, 1, s, launch_ch_combine(SEM3D_BF16X3, g, d, nullptr, nullptr, nullptr, S1, S0, S2, c, s));
+    LAUNCH_SUB(h, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S2, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+    LAUNCH_SUB(h, K_TC, K_TC_F64OUT, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, phi_np1, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+  }
+  return SEM3D_OK;
+}
+
+sem3d_status ch_check(sem3d_plan* h, double eps, double m, double dt, double S) {
+  if (!(eps > 0.0) || !(m > 0.0) || !(dt > 0.0) || !(S >= 0.0) || !std::isfinite(eps + m + dt + S))
+    return fail(SEM3D_ERR_INVALID_ARG, "need eps, m, dt > 0 and S >= 0");
+  return ensure_workspace(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+sem3d_status sem3d_ch_step(sem3d_handle h, const double* phi_n, const double* phi_nm1, double* phi_np1, double eps,
+                           double m, double dt, double S, void* stream) {
+  if (!h || !phi_n || !phi_nm1 || !phi_np1) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  if ((phi_np1 < phi_n + N && phi_n < phi_np1 + N) || (phi_np1 < phi_nm1 + N && phi_nm1 < phi_np1 + N))
+    return fail(SEM3D_ERR_INVALID_ARG, "phi_np1 overlaps an input");
+  sem3d_status st = ch_check(h, eps, m, dt, S);
+  if (st != SEM3D_OK) return st;
+  return ch_step_core(h, phi_n, phi_nm1, phi_np1, ChParams{eps, m, dt, S}, static_cast<cudaStream_t>(stream));
+}
+
+sem3d_status sem3d_ch_run(sem3d_handle h, double* phi_nm1, double* phi_n, int nsteps, double eps, double m, double dt,
+                          double S, void* stream) {
+  if (!h || !phi_nm1 || !phi_n) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  if (nsteps < 0) return fail(SEM3D_ERR_INVALID_ARG, "nsteps must be >= 0");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  if (phi_nm1 < phi_n + N && phi_n < phi_nm1 + N) return fail(SEM3D_ERR_INVALID_ARG, "phi arrays overlap");
+  sem3d_status st = ch_check(h, eps, m, dt, S);
+  if (st != SEM3D_OK) return st;
+  if (nsteps == 0) return SEM3D_OK;
+  if (!h->ch_buf) {
+    void* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, N * sizeof(double)));
+    h->ch_buf = static_cast<double*>(d);
+  }
+  if (!h->pcg_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->pcg_stream, cudaStreamNonBlocking));
+  const ChParams c{eps, m, dt, S};
+  // Buffers rotate: step q reads B[q%3] (phi_{n-1}) and B[(q+1)%3] (phi_n) and
+  // writes B[(q+2)%3]; three steps restore the roles, so a graph of three
+  // steps is replayed.  The run is on the plan's own stream, joined to the
+  // caller's by events (the caller's stream may be the uncapturable legacy one).
+  double* B[3] = {phi_nm1, phi_n, h->ch_buf};
+  cudaStream_t cs = static_cast<cudaStream_t>(stream), s = h->pcg_stream;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  CUDA_TRY(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } guard{ev0, ev1};
+  CUDA_TRY(cudaEventRecord(ev0, cs));
+  CUDA_TRY(cudaStreamWaitEvent(s, ev0, 0));
+  int q = 0;
+  // first step eagerly (one-time launch set-up must not happen inside a capture)
+  if ((st = ch_step_core(h, B[1], B[0], B[2], c, s)) != SEM3D_OK) return st;
+  q = 1;
+  const int full = (nsteps - q) / 3;
+  if (full > 0) {
+    const bool prof = h->profiling;
+    h->profiling = false;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < 3 && st == SEM3D_OK; ++t) {
+      const int qq = q + t;
+      st = ch_step_core(h, B[(qq + 1) % 3], B[qq % 3], B[(qq + 2) % 3], c, s);
+    }
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    h->profiling = prof;
+    if (st != SEM3D_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture(ch)");
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate(ch)");
+    for (int r = 0; r < full; ++r) {
+      ce = cudaGraphLaunch(exec, s);
+      if (ce != cudaSuccess) { cudaGraphExecDestroy(exec); return cuda_fail(ce, "cudaGraphLaunch(ch)"); }
+    }
+    cudaGraphExecDestroy(exec);
+    q += 3 * full;
+  }
+  for (; q < nsteps; ++q)
+    if ((st = ch_step_core(h, B[(q + 1) % 3], B[q % 3], B[(q + 2) % 3], c, s)) != SEM3D_OK) return st;
+  // phi_N is in B[(nsteps+1)%3], phi_{N-1} in B[nsteps%3]; move them home.
+  const size_t bytes = N * sizeof(double);
+  if (nsteps % 3 == 1) {         // (prev, last) = (phi_n, buf)
+    CUDA_TRY(cudaMemcpyAsync(phi_nm1, phi_n, bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(phi_n, h->ch_buf, bytes, cudaMemcpyDeviceToDevice, s));
+  } else if (nsteps % 3 == 2) {  // (prev, last) = (buf, phi_nm1)
+    CUDA_TRY(cudaMemcpyAsync(phi_n, phi_nm1, bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(phi_nm1, h->ch_buf, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaEventRecord(ev1, s));
+  CUDA_TRY(cudaStreamWaitEvent(cs, ev1, 0));
+  return SEM3D_OK;
+}
+
 sem3d_status sem3d_destroy(sem3d_handle h) {
   if (!h) return SEM3D_OK;
+  if (h->ch_buf) cudaFree(h->ch_buf);
   cudaError_t e = cudaDeviceSynchronize();
   if (h->pcg_buf) cudaFree(h->pcg_buf);
   if (h->pcg_sc) cudaFree(h->pcg_sc);

@@ -126,6 +126,17 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
                                        DfBuffers df = DfBuffers{nullptr, nullptr}, int nprod = 3);
 
+// ---- Cahn-Hilliard pointwise kernels (ch_kernels.cu)
+struct ChParams {
+  double eps, m, dt, S;
+};
+// tier: SEM3D_FP64 / SEM3D_FP32 (dense arrays ghat, gg of that type) or the
+// split tiers (sh, sg split arrays at pitch Px).
+cudaError_t launch_ch_prep(int tier, const Geom& g, const double* phi_n, const double* phi_nm1, void* ghat, void* gg,
+                           TcBuffers sh, TcBuffers sg, const ChParams& c, cudaStream_t s);
+cudaError_t launch_ch_combine(int tier, const Geom& g, const DevAxis* ax, const void* a1, const void* a2, void* out,
+                              TcBuffers s1, TcBuffers s2, TcBuffers so, const ChParams& c, cudaStream_t s);
+
 // ---- PCG vector kernels (pcg_kernels.cu)
 struct PcgScalars {
   double rz_old, rz_new, pq, beta, rnorm2, bnorm2;

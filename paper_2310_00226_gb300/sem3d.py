@@ -32,6 +32,8 @@ EXPORTS = (
     "sem3d_solve",
     "sem3d_apply",
     "sem3d_pcg",
+    "sem3d_ch_step",
+    "sem3d_ch_run",
     "sem3d_get_nodes",
     "sem3d_get_eigs",
     "sem3d_axis_info",
@@ -72,6 +74,9 @@ def lib() -> ctypes.CDLL:
     L.sem3d_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_pcg.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.POINTER(c_int),
                             ctypes.POINTER(c_double), c_void_p]
+    L.sem3d_ch_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double, c_double,
+                                c_void_p]
+    L.sem3d_ch_run.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_void_p]
     L.sem3d_get_nodes.argtypes = [c_void_p, c_int, c_void_p]
     L.sem3d_get_eigs.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
     L.sem3d_axis_info.argtypes = [c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
@@ -175,6 +180,17 @@ class Plan:
         if check:
             _check(st, "sem3d_pcg")
         return it.value, rr.value
+
+    def ch_step(self, phi_n, phi_nm1, phi_np1, eps: float, m: float, dt: float, S: float = 0.0, stream=None):
+        _check(lib().sem3d_ch_step(self._h, ctypes.c_void_p(_dev_ptr(phi_n, self.numel, "phi_n")),
+                                   ctypes.c_void_p(_dev_ptr(phi_nm1, self.numel, "phi_nm1")),
+                                   ctypes.c_void_p(_dev_ptr(phi_np1, self.numel, "phi_np1")), float(eps), float(m),
+                                   float(dt), float(S), ctypes.c_void_p(_stream_ptr(stream))), "sem3d_ch_step")
+
+    def ch_run(self, phi_nm1, phi_n, nsteps: int, eps: float, m: float, dt: float, S: float = 0.0, stream=None):
+        _check(lib().sem3d_ch_run(self._h, ctypes.c_void_p(_dev_ptr(phi_nm1, self.numel, "phi_nm1")),
+                                  ctypes.c_void_p(_dev_ptr(phi_n, self.numel, "phi_n")), int(nsteps), float(eps),
+                                  float(m), float(dt), float(S), ctypes.c_void_p(_stream_ptr(stream))), "sem3d_ch_run")
 
     def sync_check(self, stream=None):
         _check(lib().sem3d_sync_check(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_sync_check")

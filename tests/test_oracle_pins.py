@@ -298,3 +298,46 @@ def test_harmonic_potential_mean():
     V = harmonic_potential(s.x, s.x, s.x)
     w = s.M[:, None, None] * s.M[None, :, None] * s.M[None, None, :]
     assert abs((V * w).sum() / w.sum() - 25.0) < 1e-12
+
+
+# ---------------------------------------------------------------- Cahn-Hilliard oracle
+
+@pytest.mark.parametrize("S", [0.0, 2.0])
+def test_ch_step_linear_limit_on_eigenvector(S):
+    # For tiny phi the cube in F'(phi) = phi^3 - phi is negligible and the step
+    # is linear.  With phi_n = phi_{n-1} = v, an eigenvector of H3 (eigenvalue
+    # L = lx + ly + lz from the 1D closed forms of the pinned eigensolver), the
+    # step multiplies v by (3/2 + dt m L (1 + S)/eps) / (3/2 + dt m (eps L^2 + S L/eps)).
+    from oracle import ch_step
+    sx, sy, sz = sem_1d(2, 3, 0.0, 1.0), sem_1d(1, 6, 0.0, 1.3), sem_1d(2, 2, 0.0, 0.7)
+    i, j, l = 2, 3, 1
+    v = 1e-9 * (sz.T[:, l][:, None, None] * sy.T[:, j][None, :, None] * sx.T[:, i][None, None, :])
+    L = sx.lam[i] + sy.lam[j] + sz.lam[l]
+    eps, m, dt = 0.05, 1.0, 1e-4
+    got = ch_step(v, v, sx, sy, sz, eps, m, dt, S)
+    factor = (1.5 + dt * m * L * (1 + S) / eps) / (1.5 + dt * m * (eps * L**2 + S * L / eps))
+    np.testing.assert_allclose(got, factor * v, rtol=1e-9, atol=1e-22)
+
+
+def test_ch_step_nonlinear_term_and_energy_decay():
+    # A finite-amplitude state: the step must reduce the discrete Ginzburg-Landau
+    # energy E = eps/2 <phi, H3 phi>_M + 1/eps <F(phi), 1>_M (energy dissipation of
+    # the Cahn-Hilliard flow, which the stabilised BDF2 scheme keeps at small dt).
+    from oracle import assembled_h3, ch_step
+    s = sem_1d(2, 5, 0.0, 1.0)
+    rng = np.random.Generator(np.random.PCG64(3))
+    phi0 = 0.6 * rng.uniform(-1, 1, (s.n, s.n, s.n))
+    w = (s.M[:, None, None] * s.M[None, :, None] * s.M[None, None, :])
+    H3 = assembled_h3(s, s, s)
+    eps, m, dt, S = 0.1, 1.0, 1e-5, 2.0
+
+    def energy(phi):
+        grad = np.sum(w.reshape(-1) * phi.reshape(-1) * (H3 @ phi.reshape(-1)))
+        return 0.5 * eps * grad + np.sum(w * 0.25 * (phi**2 - 1) ** 2) / eps
+
+    prev, cur = phi0, phi0
+    energies = [energy(cur)]
+    for _ in range(5):
+        prev, cur = cur, ch_step(cur, prev, s, s, s, eps, m, dt, S)
+        energies.append(energy(cur))
+    assert all(b < a for a, b in zip(energies, energies[1:])), energies
