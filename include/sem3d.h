@@ -121,6 +121,22 @@ sem3d_status sem3d_set_workspace(sem3d_handle h, void* dptr, size_t bytes);
  * Enqueued on `stream`; no host synchronisation. */
 sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* stream);
 
+/* Many independent solves (the benchmark spec's batched workload; each problem is
+ * Section 2.4's solve on its own box, grid, degree and shift).
+ *   count : number of problems, 1 <= count <= 1024.
+ *   hs    : count distinct plans on the current device; each keeps its own
+ *           precision, sweeps and workspace.
+ *   f, u  : host arrays of count device pointers (as in sem3d_solve).
+ * When every plan is SEM3D_FP32 with the same sweep count (and count <= 64),
+ * each of the six mode-product passes of all problems runs as ONE grouped
+ * launch (per-problem descriptors in a device table); the FP64 residuals run
+ * per problem.  Otherwise the problems' solves run concurrently on a pool of
+ * streams forked from and joined to `stream`.  Asynchronous; the library's
+ * batch staging area is shared, so concurrent batched calls from several host
+ * threads are serialised internally. */
+sem3d_status sem3d_solve_batched(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
+                                 void* stream);
+
 /* Apply the discrete operator in H form: Au = c u + (H_x (+) H_y (+) H_z) u
  * (Eq. 12 with H = M^{-1} S, banded, at most 2k+1 entries per row and axis),
  * in FP64.  u, Au: device FP64 arrays, must not overlap. */

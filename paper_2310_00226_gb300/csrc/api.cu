@@ -814,6 +814,177 @@ sem3d_status sem3d_ch_run(sem3d_handle h, double* phi_nm1, double* phi_n, int ns
   return SEM3D_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Process-wide state of batched solves: a pool of streams for independent
+// problems and a staging area for the grouped launches' descriptor tables.
+struct BatchState {
+  std::mutex mu;
+  int device = -1;
+  cudaStream_t streams[8] = {};
+  void* host_table = nullptr;   // pinned
+  void* dev_table = nullptr;
+  size_t table_bytes = 0;
+  cudaEvent_t done = nullptr;   // last use of the staging area
+};
+BatchState g_batch;
+
+constexpr size_t kStageTableBytes = 64 * 1024;  // per grouped launch (>= 64 problems)
+
+sem3d_status batch_resources(int device, size_t stages) {
+  if (g_batch.device != device) {
+    // first use (or another device): streams and staging on this device
+    for (auto& st : g_batch.streams)
+      if (st) { cudaStreamDestroy(st); st = nullptr; }
+    if (g_batch.host_table) { cudaFreeHost(g_batch.host_table); g_batch.host_table = nullptr; }
+    if (g_batch.dev_table) { cudaFree(g_batch.dev_table); g_batch.dev_table = nullptr; }
+    if (g_batch.done) { cudaEventDestroy(g_batch.done); g_batch.done = nullptr; }
+    g_batch.table_bytes = 0;
+    for (auto& st : g_batch.streams) CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&g_batch.done, cudaEventDisableTiming));
+    g_batch.device = device;
+  }
+  const size_t need = stages * kStageTableBytes;
+  if (g_batch.table_bytes < need) {
+    CUDA_TRY(cudaEventSynchronize(g_batch.done));
+    if (g_batch.host_table) cudaFreeHost(g_batch.host_table);
+    if (g_batch.dev_table) cudaFree(g_batch.dev_table);
+    g_batch.host_table = g_batch.dev_table = nullptr;
+    CUDA_TRY(cudaMallocHost(&g_batch.host_table, need));
+    CUDA_TRY(cudaMalloc(&g_batch.dev_table, need));
+    g_batch.table_bytes = need;
+  }
+  // the staging area is reused: wait until the previous batch's copies ran
+  CUDA_TRY(cudaEventSynchronize(g_batch.done));
+  return SEM3D_OK;
+}
+
+// Grouped FP32 solves: each of the six passes of all problems is one launch.
+sem3d_status batched_f32(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
+                         cudaStream_t s) {
+  const int sweeps = hs[0]->sweeps;
+  const size_t stages = 6 * (size_t)(1 + sweeps);
+  sem3d_status st = batch_resources(hs[0]->device, stages);
+  if (st != SEM3D_OK) return st;
+  std::vector<Geom> geo(count);
+  std::vector<const float*> W(count);
+  std::vector<const void*> in(count);
+  std::vector<void*> out(count);
+  std::vector<const double*> lx(count), ly(count), lz(count);
+  std::vector<float*> A(count), B(count);
+  std::vector<double*> R(count);
+  for (int q = 0; q < count; ++q) {
+    sem3d_plan* h = hs[q];
+    const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    geo[q] = h->g;
+    lx[q] = h->dev[0].lam; ly[q] = h->dev[1].lam; lz[q] = h->dev[2].lam;
+    A[q] = static_cast<float*>(h->ws);
+    B[q] = reinterpret_cast<float*>(static_cast<char*>(h->ws) + align256(N * sizeof(float)));
+    R[q] = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(N * sizeof(float)));
+  }
+  size_t stage = 0;
+  auto pass = [&](int axis, int which, bool in64, bool out64, int epi, auto in_of, auto out_of) -> sem3d_status {
+    for (int q = 0; q < count; ++q) {
+      W[q] = hs[q]->dev[axis].Wf[which];
+      in[q] = in_of(q);
+      out[q] = out_of(q);
+    }
+    char* ht = static_cast<char*>(g_batch.host_table) + stage * kStageTableBytes;
+    char* dt = static_cast<char*>(g_batch.dev_table) + stage * kStageTableBytes;
+    ++stage;
+    LAUNCH(hs[0], K_F32, 1, s,
+           launch_mode_product_f32_grouped(count, geo.data(), axis, W.data(), in.data(), in64, out.data(), out64, epi,
+                                           lx.data(), ly.data(), lz.data(), dt, kStageTableBytes, ht, s));
+    return SEM3D_OK;
+  };
+  auto solve_group = [&](auto src, bool accumulate) -> sem3d_status {
+    sem3d_status r;
+    if ((r = pass(2, 0, true, false, EPI_STORE, src, [&](int q) -> void* { return A[q]; })) != SEM3D_OK) return r;
+    if ((r = pass(1, 0, false, false, EPI_STORE, [&](int q) -> const void* { return A[q]; },
+                  [&](int q) -> void* { return B[q]; })) != SEM3D_OK) return r;
+    if ((r = pass(0, 0, false, false, EPI_DIV, [&](int q) -> const void* { return B[q]; },
+                  [&](int q) -> void* { return A[q]; })) != SEM3D_OK) return r;
+    if ((r = pass(0, 1, false, false, EPI_STORE, [&](int q) -> const void* { return A[q]; },
+                  [&](int q) -> void* { return B[q]; })) != SEM3D_OK) return r;
+    if ((r = pass(1, 1, false, false, EPI_STORE, [&](int q) -> const void* { return B[q]; },
+                  [&](int q) -> void* { return A[q]; })) != SEM3D_OK) return r;
+    return pass(2, 1, false, true, accumulate ? EPI_ACCUM : EPI_STORE, [&](int q) -> const void* { return A[q]; },
+                [&](int q) -> void* { return u[q]; });
+  };
+  if ((st = solve_group([&](int q) -> const void* { return f[q]; }, false)) != SEM3D_OK) return st;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int q = 0; q < count; ++q) {
+      sem3d_plan* h = hs[q];
+      LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u[q], f[q], R[q], nullptr, nullptr, 1, s));
+    }
+    if ((st = solve_group([&](int q) -> const void* { return R[q]; }, true)) != SEM3D_OK) return st;
+  }
+  CUDA_TRY(cudaEventRecord(g_batch.done, s));
+  return SEM3D_OK;
+}
+
+// Any tiers: each problem's own solve on a pool of streams, forked from and
+// joined back to the caller's stream.
+sem3d_status batched_streams(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
+                             cudaStream_t s) {
+  sem3d_status st = batch_resources(hs[0]->device, 1);
+  if (st != SEM3D_OK) return st;
+  cudaEvent_t fork = nullptr;
+  CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  std::vector<cudaEvent_t> joins(8, nullptr);
+  struct Guard {
+    cudaEvent_t f;
+    std::vector<cudaEvent_t>& j;
+    ~Guard() {
+      cudaEventDestroy(f);
+      for (auto e : j)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{fork, joins};
+  CUDA_TRY(cudaEventRecord(fork, s));
+  const int ns = count < 8 ? count : 8;
+  for (int k = 0; k < ns; ++k) {
+    CUDA_TRY(cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming));
+    CUDA_TRY(cudaStreamWaitEvent(g_batch.streams[k], fork, 0));
+  }
+  for (int q = 0; q < count; ++q)
+    if ((st = run_solve(hs[q], f[q], u[q], g_batch.streams[q % ns])) != SEM3D_OK) return st;
+  for (int k = 0; k < ns; ++k) {
+    CUDA_TRY(cudaEventRecord(joins[k], g_batch.streams[k]));
+    CUDA_TRY(cudaStreamWaitEvent(s, joins[k], 0));
+  }
+  return SEM3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sem3d_status sem3d_solve_batched(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
+                                 void* stream) {
+  if (count < 1 || count > 1024 || !hs || !f || !u) return fail(SEM3D_ERR_INVALID_ARG, "bad batch arguments");
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  for (int q = 0; q < count; ++q) {
+    if (!hs[q] || !f[q] || !u[q]) return fail(SEM3D_ERR_INVALID_ARG, "NULL entry in batch");
+    if (hs[q]->device != cur) return fail(SEM3D_ERR_INVALID_ARG, "all plans must be on the current device");
+    for (int r = 0; r < q; ++r)
+      if (hs[r] == hs[q]) return fail(SEM3D_ERR_INVALID_ARG, "a plan appears twice in the batch");
+    const size_t N = (size_t)hs[q]->g.nx * hs[q]->g.ny * hs[q]->g.nz;
+    if (f[q] < u[q] + N && u[q] < f[q] + N) return fail(SEM3D_ERR_INVALID_ARG, "f and u overlap");
+    sem3d_status st = ensure_workspace(hs[q]);
+    if (st != SEM3D_OK) return st;
+  }
+  std::lock_guard<std::mutex> lk(g_batch.mu);
+  bool grouped = count <= 64;
+  for (int q = 0; q < count && grouped; ++q)
+    grouped = hs[q]->prec == SEM3D_FP32 && hs[q]->sweeps == hs[0]->sweeps;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return grouped ? batched_f32(count, hs, f, u, s) : batched_streams(count, hs, f, u, s);
+}
+
 sem3d_status sem3d_destroy(sem3d_handle h) {
   if (!h) return SEM3D_OK;
   if (h->ch_buf) cudaFree(h->ch_buf);

@@ -26,15 +26,16 @@ struct F32Pass {
   double c;
 };
 
+// One 128 x 128 output tile (row tile bx, output tile by) of pass p.
 template <typename TIN, typename TOUT, bool KCONTIG>
-__global__ void __launch_bounds__(256) mode_product_f32_kernel(F32Pass p) {
+__device__ __forceinline__ void f32_tile(const F32Pass& p, long long bx, int by) {
   __shared__ __align__(16) float As[F32_BK][F32_BM + 4];
   __shared__ __align__(16) float Ws[F32_BK][F32_BN + 4];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;  // outputs tx*8.., rows ty*8..
   const long long rows = (long long)p.R1 * p.R2;
-  const long long row0 = (long long)blockIdx.x * F32_BM;
-  const int o0 = blockIdx.y * F32_BN;
+  const long long row0 = bx * F32_BM;
+  const int o0 = by * F32_BN;
   const TIN* in = static_cast<const TIN*>(p.in);
 
   float acc[8][8];
@@ -118,6 +119,37 @@ __global__ void __launch_bounds__(256) mode_product_f32_kernel(F32Pass p) {
   }
 }
 
+template <typename TIN, typename TOUT, bool KCONTIG>
+__global__ void __launch_bounds__(256) mode_product_f32_kernel(F32Pass p) {
+  f32_tile<TIN, TOUT, KCONTIG>(p, blockIdx.x, blockIdx.y);
+}
+
+// Grouped launch: one pass (the same axis and operand types) of many
+// independent problems in a single grid.  Block b belongs to the problem q
+// with block_begin[q] <= b < block_begin[q+1]; its tiles are numbered row
+// tile fastest.
+struct F32Group {
+  int count;
+  const F32Pass* passes;
+  const long long* block_begin;  // count + 1 entries
+};
+
+template <typename TIN, typename TOUT, bool KCONTIG>
+__global__ void __launch_bounds__(256) mode_product_f32_grouped_kernel(F32Group g) {
+  __shared__ int prob;
+  if (threadIdx.x == 0) {
+    int q = 0;
+    while (q + 1 < g.count && g.block_begin[q + 1] <= (long long)blockIdx.x) ++q;
+    prob = q;
+  }
+  __syncthreads();
+  const F32Pass p = g.passes[prob];
+  const long long lb = (long long)blockIdx.x - g.block_begin[prob];
+  const long long rows = (long long)p.R1 * p.R2;
+  const long long rt = (rows + F32_BM - 1) / F32_BM;
+  f32_tile<TIN, TOUT, KCONTIG>(p, lb % rt, (int)(lb / rt));
+}
+
 template <typename TIN, typename TOUT>
 cudaError_t launch_f32(const F32Pass& p, bool kcontig, cudaStream_t s) {
   const long long rows = (long long)p.R1 * p.R2;
@@ -127,7 +159,68 @@ cudaError_t launch_f32(const F32Pass& p, bool kcontig, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+F32Pass make_pass(const Geom& g, int axis, const float* W, const void* in, void* out, int epi, const double* lamx,
+                  const double* lamy, const double* lamz, bool* kcontig) {
+  F32Pass p{};
+  p.in = in;
+  p.out = out;
+  p.W = W;
+  p.epi = epi;
+  p.nx = g.nx;
+  p.ny = g.ny;
+  p.lamx = lamx;
+  p.lamy = lamy;
+  p.lamz = lamz;
+  p.c = g.c;
+  const long long nxy = (long long)g.nx * g.ny;
+  *kcontig = false;
+  if (axis == 0) {
+    p.R1 = g.ny * g.nz; p.R2 = 1; p.s1 = g.nx; p.s2 = 0; p.sm = 1; p.n = g.nx; *kcontig = true;
+  } else if (axis == 1) {
+    p.R1 = g.nx; p.R2 = g.nz; p.s1 = 1; p.s2 = nxy; p.sm = g.nx; p.n = g.ny;
+  } else {
+    p.R1 = (int)nxy; p.R2 = 1; p.s1 = 1; p.s2 = 0; p.sm = nxy; p.n = g.nz;
+  }
+  return p;
+}
+
+template <typename TIN, typename TOUT>
+cudaError_t launch_f32_grouped(const F32Group& grp, long long blocks, bool kcontig, cudaStream_t s) {
+  if (kcontig) mode_product_f32_grouped_kernel<TIN, TOUT, true><<<(unsigned)blocks, 256, 0, s>>>(grp);
+  else mode_product_f32_grouped_kernel<TIN, TOUT, false><<<(unsigned)blocks, 256, 0, s>>>(grp);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_mode_product_f32_grouped(int count, const Geom* geoms, int axis, const float* const* W,
+                                            const void* const* in, bool in_f64, void* const* out, bool out_f64,
+                                            int epi, const double* const* lamx, const double* const* lamy,
+                                            const double* const* lamz, void* dev_table, size_t table_bytes,
+                                            void* host_table, cudaStream_t s) {
+  // Table layout: count passes, then count + 1 block offsets.
+  const size_t need = (size_t)count * sizeof(F32Pass) + (size_t)(count + 1) * sizeof(long long);
+  if (count < 1 || need > table_bytes) return cudaErrorInvalidValue;
+  if (epi == EPI_ACCUM && !out_f64) return cudaErrorInvalidValue;
+  F32Pass* passes = static_cast<F32Pass*>(host_table);
+  long long* begin = reinterpret_cast<long long*>(static_cast<char*>(host_table) + (size_t)count * sizeof(F32Pass));
+  bool kcontig = false;
+  begin[0] = 0;
+  for (int q = 0; q < count; ++q) {
+    passes[q] = make_pass(geoms[q], axis, W[q], in[q], out[q], epi, lamx[q], lamy[q], lamz[q], &kcontig);
+    const long long rows = (long long)passes[q].R1 * passes[q].R2;
+    begin[q + 1] = begin[q] + ((rows + F32_BM - 1) / F32_BM) * ((passes[q].n + F32_BN - 1) / F32_BN);
+  }
+  if (begin[count] >= (1LL << 31)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(dev_table, host_table, need, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  F32Group grp{count, static_cast<const F32Pass*>(dev_table),
+               reinterpret_cast<const long long*>(static_cast<const char*>(dev_table) + (size_t)count * sizeof(F32Pass))};
+  if (in_f64 && out_f64) return launch_f32_grouped<double, double>(grp, begin[count], kcontig, s);
+  if (in_f64) return launch_f32_grouped<double, float>(grp, begin[count], kcontig, s);
+  if (out_f64) return launch_f32_grouped<float, double>(grp, begin[count], kcontig, s);
+  return launch_f32_grouped<float, float>(grp, begin[count], kcontig, s);
+}
 
 cudaError_t launch_mode_product_f32(const Geom& g, int axis, const float* W, const void* in, bool in_f64, void* out,
                                     bool out_f64, int epi, const double* lamx, const double* lamy, const double* lamz,

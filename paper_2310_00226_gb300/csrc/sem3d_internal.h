@@ -97,6 +97,14 @@ cudaError_t launch_mode_product_f64(const Geom& g, int axis, const double* W, co
 cudaError_t launch_mode_product_f32(const Geom& g, int axis, const float* W, const void* in, bool in_f64, void* out,
                                     bool out_f64, int epi, const double* lamx, const double* lamy, const double* lamz,
                                     cudaStream_t s);
+// The same pass for `count` independent problems in one grouped launch.
+// The per-problem descriptor table (count * ~160 B) is staged through
+// host_table (pinned, >= table_bytes) into dev_table with an async copy on s.
+cudaError_t launch_mode_product_f32_grouped(int count, const Geom* geoms, int axis, const float* const* W,
+                                            const void* const* in, bool in_f64, void* const* out, bool out_f64,
+                                            int epi, const double* const* lamx, const double* const* lamy,
+                                            const double* const* lamz, void* dev_table, size_t table_bytes,
+                                            void* host_table, cudaStream_t s);
 // Au = c u + (H_x (+) H_y (+) H_z) u            (mode 0)
 // r  = f - c u - (H_x (+) H_y (+) H_z) u        (mode 1, FP64 r)
 // r  = same, written as bf16 hi/lo at pitch Px   (mode 2)

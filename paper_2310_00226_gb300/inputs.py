@@ -133,3 +133,20 @@ def schrodinger_manufactured(x, y, z, amp: float = 100.0):
     u = _outer3(np.sin(PI * np.asarray(x)), np.sin(PI * np.asarray(y)), np.sin(PI * np.asarray(z)))
     V = harmonic_potential(x, y, z, amp)
     return u, V, (3 * PI**2 + V) * u
+
+
+def batched_helmholtz(count: int = 64, seed: int = 20231001, sizes=(63, 127, 255, 383, 511), degrees=(2, 3, 4, 6)):
+    """Problem list of the batched workload: for problem i a PCG64 generator
+    seeded with seed + i draws k from `degrees`, each axis size uniformly from
+    the entries of `sizes` with (n + 1) % k == 0, and c uniform in [0, 10].
+    Boxes are [0,1]^3.  Returns dicts with n3, k, c and the seed of its f
+    (i.i.d. N(0,1) from random_rhs)."""
+    out = []
+    for i in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed + i))
+        k = int(rng.choice(np.asarray(degrees)))
+        allowed = np.asarray([n for n in sizes if (n + 1) % k == 0])
+        n3 = tuple(int(rng.choice(allowed)) for _ in range(3))
+        c = float(rng.uniform(0.0, 10.0))
+        out.append({"n3": n3, "k": k, "c": c, "seed": seed + 1000 + i})
+    return out

@@ -30,6 +30,7 @@ EXPORTS = (
     "sem3d_workspace_size",
     "sem3d_set_workspace",
     "sem3d_solve",
+    "sem3d_solve_batched",
     "sem3d_apply",
     "sem3d_pcg",
     "sem3d_ch_step",
@@ -72,6 +73,8 @@ def lib() -> ctypes.CDLL:
     L.sem3d_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
     L.sem3d_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_solve_batched.argtypes = [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                      ctypes.POINTER(c_void_p), c_void_p]
     L.sem3d_pcg.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.POINTER(c_int),
                             ctypes.POINTER(c_double), c_void_p]
     L.sem3d_ch_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double, c_double,
@@ -123,6 +126,17 @@ def axis_info(n: int, k: int, L: float = 1.0):
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
     _check(lib().sem3d_axis_info(n, k, float(L), ptr(x), ptr(M), ptr(lam), ptr(T)), "sem3d_axis_info")
     return x, M, lam, T
+
+
+def solve_batched(plans, fs, us, stream=None):
+    """sem3d_solve_batched over lists of plans and float64 CUDA tensors."""
+    n = len(plans)
+    if not (n == len(fs) == len(us)):
+        raise ValueError("plans, fs and us must have the same length")
+    H = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    F = (ctypes.c_void_p * n)(*[_dev_ptr(f, p.numel, "f") for p, f in zip(plans, fs)])
+    U = (ctypes.c_void_p * n)(*[_dev_ptr(u, p.numel, "u") for p, u in zip(plans, us)])
+    _check(lib().sem3d_solve_batched(n, H, F, U, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_solve_batched")
 
 
 class Plan:

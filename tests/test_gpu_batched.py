@@ -1,0 +1,74 @@
+"""GPU parity of sem3d_solve_batched against the oracle, problem by problem.
+
+Grouped path: every plan SEM3D_FP32 with the same sweeps (one launch per
+pass for all problems).  Stream path: mixed tiers.  Tolerance: relative L-inf
+1e-12 after refinement (2 sweeps FP32, 3 sweeps BF16x3, 1 sweep FP64).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import refined_solve, sem_1d
+from paper_2310_00226_gb300.inputs import batched_helmholtz, random_rhs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sem3d():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2310_00226_gb300 import sem3d as mod
+    mod.lib()
+    return mod
+
+
+def _problems():
+    # the batched workload's generator with small sizes (the oracle solves each in < 1 s)
+    return batched_helmholtz(count=7, seed=77, sizes=(7, 11, 15, 23, 31, 47), degrees=(2, 3, 4, 6))
+
+
+def _refs(probs):
+    refs = []
+    for pr in probs:
+        n3, k, c = pr["n3"], pr["k"], pr["c"]
+        axes = [sem_1d(k, (n + 1) // k, 0.0, 1.0) for n in n3]
+        F = random_rhs(*n3, seed=pr["seed"])
+        refs.append((F, refined_solve(F, *axes, c, sweeps=1)))
+    return refs
+
+
+@pytest.mark.parametrize("mode", ["grouped_fp32", "streams_mixed"])
+def test_batched_matches_oracle(sem3d, mode):
+    probs = _problems()
+    refs = _refs(probs)
+    plans, fs, us = [], [], []
+    try:
+        for q, pr in enumerate(probs):
+            p = sem3d.Plan(*pr["n3"], pr["k"], (1.0, 1.0, 1.0), pr["c"])
+            if mode == "grouped_fp32":
+                p.set_precision("fp32", 2)
+            else:
+                p.set_precision(*[("fp32", 2), ("bf16x3", 3), ("fp64", 1)][q % 3])
+            plans.append(p)
+            fs.append(torch.from_numpy(refs[q][0]).cuda())
+            us.append(torch.full_like(fs[-1], float("nan")))
+        for _ in range(2):  # twice: the staging area is reused
+            sem3d.solve_batched(plans, fs, us)
+            plans[0].sync_check()
+            for q in range(len(probs)):
+                got = us[q].cpu().numpy()
+                ref = refs[q][1]
+                assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12, (mode, q, probs[q])
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batched_rejects_duplicate_plans(sem3d):
+    with sem3d.Plan(7, 7, 7, 2) as p:
+        f = torch.zeros(343, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(f)
+        with pytest.raises(sem3d.Sem3dError):
+            sem3d.solve_batched([p, p], [f, f], [u, u])
