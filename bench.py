@@ -345,6 +345,94 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     return 0
 
 
+# --------------------------------------------------------------------- other workloads
+
+def _timed_host(fn, steps, warmup, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3 / steps
+
+
+def run_workload(args, rank: int):
+    """Batched Helmholtz, Cahn-Hilliard and Schroedinger-PCG workloads (one JSON
+    line each; not the headline metric)."""
+    import torch
+    from paper_2310_00226_gb300 import sem3d
+    from paper_2310_00226_gb300.inputs import batched_helmholtz, harmonic_potential, random_rhs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    line = {"workload": args.workload, "n_gpus": 1, "data": "synthetic", "higher_is_better": True}
+    if args.workload == "batched":
+        probs = batched_helmholtz(64)
+        plans, fs, us = [], [], []
+        for pr in probs:
+            p = sem3d.Plan(*pr["n3"], pr["k"], (1.0, 1.0, 1.0), pr["c"])
+            plans.append(p)
+            nx, ny, nz = pr["n3"]
+            fs.append(torch.from_numpy(random_rhs(nx, ny, nz, pr["seed"])).cuda())
+            us.append(torch.empty_like(fs[-1]))
+        dofs = sum(p.numel for p in plans)
+        res = {}
+        for prec, sweeps in (("fp32", 2), ("bf16x3", 3)):
+            for p in plans:
+                p.set_precision(prec, sweeps)
+            ms = _timed_host(lambda: sem3d.solve_batched(plans, fs, us, stream), args.steps, args.warmup, torch)
+            plans[0].sync_check(stream)
+            res[prec] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": sweeps,
+                         "path": "grouped launches" if prec == "fp32" else "stream pool"}
+        line.update({"metric": "64 batched Helmholtz solves (uneven n in {63..511}, k in {2,3,4,6}): GDoF/s",
+                     "value": res["fp32"]["GDoF_per_s"], "unit": "GDoF/s", "total_dofs": dofs, "tiers": res,
+                     "steps": args.steps, "warmup": args.warmup})
+    elif args.workload == "ch":
+        n, k = 511, 2
+        p = sem3d.Plan(n, n, n, k, (2 * np.pi,) * 3, 0.0)
+        rng = np.random.Generator(np.random.PCG64(20231001))
+        phi0 = torch.from_numpy(rng.uniform(-0.05, 0.05, (n, n, n))).cuda()
+        res = {}
+        for prec in ("bf16x3", "fp32"):
+            p.set_precision(prec, 0)
+            steps = args.ch_steps if prec == "bf16x3" else max(1, args.ch_steps // 10)
+            pm, pn = phi0.clone(), phi0.clone()
+            p.ch_run(pm, pn, 3, 0.05, 1.0, 1e-4, 2.0, stream)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.ch_run(pm, pn, steps, 0.05, 1.0, 1e-4, 2.0, stream)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / steps
+            p.sync_check(stream)
+            res[prec] = {"ms_per_step": ms, "steps": steps, "max_abs_phi": float(pn.abs().max())}
+        line.update({"metric": "Cahn-Hilliard BDF2 step, Q^2 n=511 on [0,2pi]^3 (1.33e8 DoF): ms/step",
+                     "value": res["bf16x3"]["ms_per_step"], "unit": "ms/step", "higher_is_better": False,
+                     "tiers": res, "params": {"eps": 0.05, "m": 1.0, "dt": 1e-4, "S": 2.0}})
+    elif args.workload == "pcg":
+        n, k = 1023, 4
+        p = sem3d.Plan(n, n, n, k, (1.0, 1.0, 1.0), 25.0)
+        x = p.nodes(0)
+        V = torch.from_numpy(harmonic_potential(x, x, x, 100.0)).cuda()
+        f = torch.ones_like(V)
+        u = torch.empty_like(V)
+        res = {}
+        for prec, sweeps in (("bf16x3", 0), ("bf16x3", 1)):
+            p.set_precision(prec, sweeps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, rr = p.pcg(V, f, u, rtol=1e-10, maxit=200, stream=stream)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            res[f"{prec}_sweeps{sweeps}"] = {"ms": ms, "iterations": it, "relres": rr, "ms_per_iteration": ms / it}
+        line.update({"metric": "Schroedinger -Lap u + 100|x-1/2|^2 u = 1, Q^4 n=1023 (1.07e9 DoF), PCG to 1e-10: s",
+                     "value": min(r["ms"] for r in res.values()) / 1e3, "unit": "s", "higher_is_better": False,
+                     "preconditioner": res})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,13 +448,18 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--oracle-lines", type=int, default=63, help="slab thickness; (lines+1) % 4 == 0")
+    ap.add_argument("--oracle-lines", type=int, default=63, help="slab thickness; (lines+1) %% 4 == 0")
+    ap.add_argument("--workload", choices=["solve", "batched", "ch", "pcg"], default="solve",
+                    help="solve = the headline n=999 solve; the others time the batched, Cahn-Hilliard and PCG workloads")
+    ap.add_argument("--ch-steps", type=int, default=1000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "solve":
+        return run_workload(args, rank)
     return run_ours(args, rank, world, local_rank)
 
 
