@@ -60,12 +60,17 @@ typedef enum {
  *   SEM3D_BF16X3 : operands split x = hi + lo into two bfloat16 numbers;
  *                  hi*hi + hi*lo + lo*hi accumulated in FP32 on tcgen05
  *                  tensor cores (about 16 significant bits per pass).
+ *   SEM3D_F16X3  : the same three products on fp16 hi + lo pairs (about 22
+ *                  significant bits per pass) of arrays scaled by powers of
+ *                  two chosen on the device from tracked maxima (fp16's
+ *                  range is small); needs k <= 8.
  * FP64 accuracy is recovered by iterative refinement (sem3d_set_precision). */
 typedef enum {
   SEM3D_FP64 = 0,
   SEM3D_FP32 = 1,
   SEM3D_BF16 = 4,
-  SEM3D_BF16X3 = 5
+  SEM3D_BF16X3 = 5,
+  SEM3D_F16X3 = 6
 } sem3d_precision;
 
 /* Build a plan: 1D GLL nodes, stiffness S, lumped mass M and the robust
@@ -90,7 +95,7 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
  * With a fixed sweep count the solve performs no host synchronisation. */
 sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
 
-/* Arithmetic of the refinement residuals in the SEM3D_BF16X3 tier.
+/* Arithmetic of the refinement residuals in the SEM3D_BF16X3 / F16X3 tiers.
  *   SEM3D_RESIDUAL_FP64  : every sweep computes r = f - (c + H_x (+) H_y (+)
  *                          H_z) u in FP64 with the banded operator of Eq. 12.
  *   SEM3D_RESIDUAL_MIXED : (default) sweeps 1 .. s-1 compute it in double-FP32

@@ -71,6 +71,8 @@ struct sem3d_plan {
   size_t ws_bytes = 0;
   bool ws_owned = false;
   int* d_err = nullptr;
+  F16State* d_f16 = nullptr;  // scale state of the F16X3 tier
+  float div_bound = 1.f;      // 1 / (lambda_x,1 + lambda_y,1 + lambda_z,1 + c)
   std::vector<void*> owned;  // device allocations made at setup
   // launch accounting and optional per-kernel timing
   unsigned long long launches = 0;
@@ -232,22 +234,28 @@ sem3d_status solve_once_bf16x3(sem3d_plan* p, TcBuffers S0, TcBuffers S1, double
                                cudaStream_t s) {
   const int np = (p->prec == SEM3D_BF16) ? 1 : 3;
   const DfBuffers none{nullptr, nullptr};
+  // F16X3: pass q reads scale slot q-1 and writes slot q (slot 0 = split input).
+  const bool f16 = p->prec == SEM3D_F16X3;
+  F16Pass fp[6];
+  for (int q = 0; q < 6; ++q) fp[q] = F16Pass{p->d_f16, q, q + 1, q == 2 ? p->div_bound : 1.f};
+  const F16Pass* F[6];
+  for (int q = 0; q < 6; ++q) F[q] = f16 ? &fp[q] : nullptr;
   const Geom& g = p->g;
   const DevAxis* d = p->dev;
   const float *lx = d[0].lamf, *ly = d[1].lamf, *lz = d[2].lamf;
   const int sms = p->num_sms;
   int* e = p->d_err;
   // Forward: z, y, x with the division fused into the x pass (Eq. 13).
-  LAUNCH_SUB(p, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
-  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
-  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s, none, np));
+  LAUNCH_SUB(p, K_TC, K_TC_Z, 1, s, launch_mode_product_bf16x3(g, 2, d[2], 0, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np, F[0]));
+  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 0, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np, F[1]));
+  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 0, S0, S1, nullptr, EPI_DIV, lx, ly, lz, e, sms, s, none, np, F[2]));
   // Backward: x, y, z.  The mode products commute, so the order is free; the
   // z pass goes last because its TMEM lanes run along the contiguous index,
   // which makes the read-modify-write of the solution coalesced.
-  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
-  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np));
+  LAUNCH_SUB(p, K_TC, K_TC_X, 1, s, launch_mode_product_bf16x3(g, 0, d[0], 1, S1, S0, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np, F[3]));
+  LAUNCH_SUB(p, K_TC, K_TC_Y, 1, s, launch_mode_product_bf16x3(g, 1, d[1], 1, S0, S1, nullptr, EPI_STORE, lx, ly, lz, e, sms, s, none, np, F[4]));
   LAUNCH_SUB(p, K_TC, K_TC_F64OUT, 1, s,
-             launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out64, epi_last, lx, ly, lz, e, sms, s, df, np));
+             launch_mode_product_bf16x3(g, 2, d[2], 1, S1, S0, out64, epi_last, lx, ly, lz, e, sms, s, df, np, F[5]));
   return SEM3D_OK;
 }
 
@@ -319,6 +327,33 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
       std::vector<float> wf(Wd.begin(), Wd.end());
       if ((st = dev_upload(p.get(), &D.Wf[w], wf.data(), wf.size())) != SEM3D_OK) return st;
     }
+    for (int w = 0; w < 2; ++w) {  // fp16 pairs of W * 2^eW for the F16X3 tier
+      const std::vector<double>& Wd = (w == 0) ? A.Tinv : A.T;
+      const int n = A.n;
+      double mx = 0.0, norm = 0.0;
+      for (int o = 0; o < n; ++o) {
+        double rs = 0.0;
+        for (int t = 0; t < n; ++t) {
+          const double v = std::fabs(Wd[(size_t)o * n + t]);
+          mx = std::max(mx, v);
+          rs += v;
+        }
+        norm = std::max(norm, rs);
+      }
+      const int eW = mx > 0.0 ? std::ilogb(16384.0 / mx) : 0;
+      D.eW16[w] = eW;
+      D.normW[w] = (float)norm;
+      std::vector<__half> h16((size_t)n * D.Kp, __float2half_rn(0.f)), l16((size_t)n * D.Kp, __float2half_rn(0.f));
+      for (int o = 0; o < n; ++o)
+        for (int t = 0; t < n; ++t) {
+          const float x = (float)std::ldexp(Wd[(size_t)o * n + t], eW);
+          const __half hh = __float2half_rn(x);
+          h16[(size_t)o * D.Kp + t] = hh;
+          l16[(size_t)o * D.Kp + t] = __float2half_rn(x - __half2float(hh));
+        }
+      if ((st = dev_upload(p.get(), &D.W16_hi[w], h16.data(), h16.size())) != SEM3D_OK) return st;
+      if ((st = dev_upload(p.get(), &D.W16_lo[w], l16.data(), l16.size())) != SEM3D_OK) return st;
+    }
     std::vector<__nv_bfloat16> hi, lo;
     for (int w = 0; w < 2; ++w) {
       split_matrix(w == 0 ? A.Tinv : A.T, A.n, D.Kp, hi, lo);
@@ -332,17 +367,20 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
     p->owned.push_back(d);
     CUDA_TRY(cudaMemset(d, 0, 256));
     p->d_err = static_cast<int*>(d);
+    p->d_f16 = reinterpret_cast<F16State*>(static_cast<char*>(d) + 128);
   }
+  p->div_bound = (float)(1.0 / (lmin + c));
   *out = p.release();
   return SEM3D_OK;
 }
 
 sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweeps) {
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
-  if (prec != SEM3D_FP64 && prec != SEM3D_FP32 && prec != SEM3D_BF16 && prec != SEM3D_BF16X3)
+  if (prec != SEM3D_FP64 && prec != SEM3D_FP32 && prec != SEM3D_BF16 && prec != SEM3D_BF16X3 && prec != SEM3D_F16X3)
     return fail(SEM3D_ERR_INVALID_ARG, "unknown precision");
+  if (prec == SEM3D_F16X3 && h->k > 8) return fail(SEM3D_ERR_UNSUPPORTED, "F16X3 needs k <= 8");
   if (sweeps < 0 || sweeps > 16) return fail(SEM3D_ERR_INVALID_ARG, "sweeps must be in [0, 16]");
-  if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16) {
+  if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16 || prec == SEM3D_F16X3) {
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
@@ -419,15 +457,39 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
     const int sw = h->sweeps;
     // Mixed residuals: sweeps 1 .. sw-1 in double-FP32 with the solution held
     // as a double-FP32 pair, the last sweep in FP64 on the FP64 solution.
-    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8 && h->prec == SEM3D_BF16X3;
-    LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s));
+    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8 &&
+                       (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_F16X3);
+    const bool f16 = h->prec == SEM3D_F16X3;
+    // F16X3: the residual is written as FP32 into S1's storage (4 bytes per
+    // entry at pitch Px fit in its hi + lo arrays) and then split with a
+    // power-of-two scale chosen from its maximum.
+    float* r32 = reinterpret_cast<float*>(S1.hi);
+    __half* S0h = reinterpret_cast<__half*>(S0.hi);
+    __half* S0l = reinterpret_cast<__half*>(S0.lo);
+    auto reset_scales = [&]() -> sem3d_status {
+      CUDA_TRY(cudaMemsetAsync(h->d_f16, 0, sizeof(F16State), s));
+      return SEM3D_OK;
+    };
+    if (f16) {
+      if ((st = reset_scales()) != SEM3D_OK) return st;
+      LAUNCH(h, K_SPLIT, 1, s, launch_absmax_f64(h->g, f, h->d_f16, s));
+      LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, f, true, S0h, S0l, h->d_f16, s));
+    } else {
+      LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s));
+    }
     if (!mixed) {
       if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_STORE, none, s)) != SEM3D_OK) return st;
     } else {
       if ((st = solve_once_bf16x3(h, S0, S1, nullptr, EPI_DF_STORE, D, s)) != SEM3D_OK) return st;
       for (int q = 1; q < sw; ++q) {
-        LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
-               launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
+        if (f16) {
+          if ((st = reset_scales()) != SEM3D_OK) return st;
+          LAUNCH(h, K_STENCIL, 1, s, launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16));
+          LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
+        } else {
+          LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
+                 launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
+        }
         const bool last_df = (q == sw - 1);
         if ((st = solve_once_bf16x3(h, S0, S1, last_df ? u : nullptr, last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, D,
                                     s)) != SEM3D_OK)
@@ -435,8 +497,14 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
       }
     }
     for (int q = mixed ? sw - 1 : 0; q < sw; ++q) {
-      LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
-             launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
+      if (f16) {
+        if ((st = reset_scales()) != SEM3D_OK) return st;
+        LAUNCH(h, K_STENCIL, 1, s, launch_stencil_f32out(h->g, h->k, h->dev, u, f, r32, h->d_f16, s));
+        LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
+      } else {
+        LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
+               launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
+      }
       if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_ACCUM, none, s)) != SEM3D_OK) return st;
     }
   }

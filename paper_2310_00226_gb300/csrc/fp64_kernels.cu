@@ -136,7 +136,15 @@ struct StencilArgs {
   const int *lox, *hix, *loy, *hiy, *loz, *hiz;
   int nx, ny, nz, k, Px, mode;
   double c;
+  float* out32;        // MODE 3: FP32 residual at pitch Px, max |r| -> st slot 0
+  F16State* st;
 };
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
 
 __global__ void __launch_bounds__(256) stencil_kernel(StencilArgs a) {
   const long long N = (long long)a.nx * a.ny * a.nz;
@@ -204,6 +212,7 @@ __global__ void __launch_bounds__(256) stencil_elem_kernel(StencilArgs a, const 
   const long long lines = (long long)a.ny * a.nz;
   const long long total = (long long)nex * lines;
   const long long plane = (long long)a.nx * a.ny;
+  float rmax = 0.f;  // MODE 3: max |r| of this thread's nodes
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int ex = (int)(t % nex);
@@ -271,6 +280,17 @@ __global__ void __launch_bounds__(256) stencil_elem_kernel(StencilArgs a, const 
         }
       }
     }
+    if (MODE == 3) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const int i = i0 + q;
+        if (i < 0) continue;
+        const float rf = (float)acc[q];
+        a.out32[(long long)i + (long long)a.Px * jl] = rf;
+        rmax = fmaxf(rmax, fabsf(rf));
+      }
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int i = i0 + q;
@@ -287,6 +307,10 @@ __global__ void __launch_bounds__(256) stencil_elem_kernel(StencilArgs a, const 
       }
     }
   }
+  if (MODE == 3) {  // every lane of the warp gets here (after the loop)
+    rmax = warp_max(rmax);
+    if ((threadIdx.x & 31) == 0 && rmax > 0.f) atomicMax(&a.st->maxbits[0], __float_as_uint(rmax));
+  }
 }
 
 template <int K>
@@ -301,7 +325,8 @@ cudaError_t launch_elem(const StencilArgs& a, const DevAxis* ax, int mode, cudaS
   const int grid = (int)(b < 1 ? 1 : b);
   if (mode == 0) stencil_elem_kernel<K, 0><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
   else if (mode == 1) stencil_elem_kernel<K, 1><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
-  else stencil_elem_kernel<K, 2><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
+  else if (mode == 2) stencil_elem_kernel<K, 2><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
+  else stencil_elem_kernel<K, 3><<<grid, 256, 0, s>>>(a, ax[0].Hq, ax[1].Hq, ax[2].Hq, nex);
   return cudaGetLastError();
 }
 
@@ -348,6 +373,8 @@ struct DfArgs {
   const double* f;
   __nv_bfloat16* hi;
   __nv_bfloat16* lo;
+  float* out32;        // if set: FP32 residual at pitch Px, max |r| -> st slot 0
+  F16State* st;
   const float *Hxh, *Hxl, *Hyh, *Hyl, *Hzh, *Hzl;
   int nx, ny, nz, Px, nex;
 };
@@ -358,6 +385,7 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
   const long long lines = (long long)a.ny * a.nz;
   const long long total = (long long)a.nex * lines;
   const long long plane = (long long)a.nx * a.ny;
+  float rmax = 0.f;  // FP32 output: max |r| of this thread's nodes
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int ex = (int)(t % a.nex);
@@ -420,6 +448,17 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
         }
       }
     }
+    if (a.out32) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const int i = i0 + q;
+        if (i < 0) continue;
+        const float rf = ah[q] + al[q];
+        a.out32[(long long)i + (long long)a.Px * jl] = rf;
+        rmax = fmaxf(rmax, fabsf(rf));
+      }
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int i = i0 + q;
@@ -431,6 +470,10 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
       a.hi[o] = h16;
       a.lo[o] = l16;
     }
+  }
+  if (a.out32) {  // every lane of the warp gets here (after the loop)
+    rmax = warp_max(rmax);
+    if ((threadIdx.x & 31) == 0 && rmax > 0.f) atomicMax(&a.st->maxbits[0], __float_as_uint(rmax));
   }
 }
 
@@ -545,9 +588,11 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 }
 
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
-                              __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s) {
+                              __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s, float* out32,
+                              F16State* st) {
   DfArgs a{};
   a.uh = u.hi; a.ul = u.lo; a.f = f; a.hi = out_hi; a.lo = out_lo;
+  a.out32 = out32; a.st = st;
   a.Hxh = ax[0].Hq_hi; a.Hxl = ax[0].Hq_lo;
   a.Hyh = ax[1].Hq_hi; a.Hyl = ax[1].Hq_lo;
   a.Hzh = ax[2].Hq_hi; a.Hzl = ax[2].Hq_lo;
@@ -565,9 +610,77 @@ cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers
     case 8: e = launch_df<8>(a, s); break;
     default: return cudaErrorInvalidValue;
   }
-  if (e != cudaSuccess || g.Px == g.nx) return e;
+  if (e != cudaSuccess || g.Px == g.nx || out32) return e;
   const long long lines = (long long)g.ny * g.nz;
   zero_pads_kernel<<<grid_for(lines * (g.Px - g.nx), 256), 256, 0, s>>>(out_hi, out_lo, g.nx, g.Px, lines);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_f32out(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f,
+                                  float* out32, F16State* st, cudaStream_t s) {
+  if (k < 1 || k > 8) return cudaErrorInvalidValue;
+  StencilArgs a{};
+  a.u = u; a.f = f; a.out32 = out32; a.st = st;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.k = k; a.Px = g.Px; a.mode = 3; a.c = g.c;
+  switch (k) {
+    case 1: return launch_elem<1>(a, ax, 3, s);
+    case 2: return launch_elem<2>(a, ax, 3, s);
+    case 3: return launch_elem<3>(a, ax, 3, s);
+    case 4: return launch_elem<4>(a, ax, 3, s);
+    case 5: return launch_elem<5>(a, ax, 3, s);
+    case 6: return launch_elem<6>(a, ax, 3, s);
+    case 7: return launch_elem<7>(a, ax, 3, s);
+    default: return launch_elem<8>(a, ax, 3, s);
+  }
+}
+
+// ------------------------------------------------------------------ F16X3 split
+__global__ void __launch_bounds__(256) absmax_f64_kernel(const double* in, long long N, F16State* st) {
+  float m = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, (float)fabs(in[i]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&st->maxbits[0], __float_as_uint(m));
+}
+
+// hi + lo = fp16 split of x * 2^e, e from slot 0's max (largest |x 2^e| near
+// 2^15 < 65504); fp16 subnormals keep the absolute error below 2^-24 of 2^e.
+template <bool IN64>
+__global__ void __launch_bounds__(256) split_f16_kernel(const void* in, __half* hi, __half* lo, int nx, int Px,
+                                                        long long lines, F16State* st) {
+  const float mx = __uint_as_float(st->maxbits[0]);
+  int e = 0;
+  if (mx > 0.f && isfinite(mx)) {
+    e = ilogbf(32768.f / mx);
+    e = e < -120 ? -120 : (e > 120 ? 120 : e);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->e[0] = e;
+  const float sc = __int_as_float((e + 127) << 23);
+  const long long total = lines * Px;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long line = idx / Px;
+    const int i = (int)(idx - line * Px);
+    float x = 0.f;
+    if (i < nx) x = IN64 ? (float)static_cast<const double*>(in)[line * nx + i] : static_cast<const float*>(in)[idx];
+    x *= sc;
+    const __half h = __float2half_rn(x);
+    hi[idx] = h;
+    lo[idx] = __float2half_rn(x - __half2float(h));
+  }
+}
+
+cudaError_t launch_absmax_f64(const Geom& g, const double* in, F16State* st, cudaStream_t s) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  absmax_f64_kernel<<<grid_for(N, 256), 256, 0, s>>>(in, N, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_f16(const Geom& g, const void* in, bool in_f64, __half* hi, __half* lo, F16State* st,
+                             cudaStream_t s) {
+  const long long lines = (long long)g.ny * g.nz;
+  if (in_f64) split_f16_kernel<true><<<grid_for(lines * g.Px, 256), 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines, st);
+  else split_f16_kernel<false><<<grid_for(lines * g.Px, 256), 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines, st);
   return cudaGetLastError();
 }
 

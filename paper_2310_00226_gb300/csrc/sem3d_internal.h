@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda.h>
 
 #include <cstdint>
@@ -59,6 +60,12 @@ struct DevAxis {
   int* band_hi = nullptr;
   float* Wf[2] = {nullptr, nullptr};            // FP32 copies: [0] = T^{-1}, [1] = T; n x n row-major
   __nv_bfloat16* W_hi[2] = {nullptr, nullptr};  // [0] = T^{-1}, [1] = T; n rows x Kp
+  // F16X3 tier: W * 2^eW16 split into fp16 hi + lo (same layout), and the
+  // infinity norm of W (largest row sum of |W|) for the scale bounds.
+  __half* W16_hi[2] = {nullptr, nullptr};
+  __half* W16_lo[2] = {nullptr, nullptr};
+  int eW16[2] = {0, 0};
+  float normW[2] = {0.f, 0.f};
   __nv_bfloat16* W_lo[2] = {nullptr, nullptr};
 };
 
@@ -70,6 +77,26 @@ enum Epi : int {
   EPI_DF_STORE = 3,    // double-FP32 solution (hi, lo) = (acc, 0)            [z pass]
   EPI_DF_ACCUM = 4,    // (hi, lo) += acc                                     [z pass]
   EPI_DF_ACCUM_F64 = 5 // FP64 out = (hi, lo) + acc                           [z pass]
+};
+
+// Power-of-two scaling of the fp16 split arrays of the F16X3 tier, kept on
+// the device so a solve needs no host round trip.  Slot 0 describes the split
+// input of a solve, slot p the output of its p-th mode product: e[p] is the
+// exponent of the scale 2^e the array is stored with, maxbits[p] the FP32 bit
+// pattern of the largest |value| (unscaled) written to it (atomicMax on the
+// bits orders non-negative floats correctly).
+struct F16State {
+  int e[8];
+  unsigned int maxbits[8];
+};
+
+// F16X3 operands: the pass reads state slot pin and writes slot pout; the
+// division bound is 1 / min(lambda_x + lambda_y + lambda_z + c) for the
+// pass with the lambda-sum division (1 otherwise).
+struct F16Pass {
+  F16State* st;
+  int pin, pout;
+  float div_bound;
 };
 
 // Solution in double-FP32 form between refinement sweeps: u = hi + lo.
@@ -115,7 +142,12 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 // bf16 hi/lo at pitch Px.  Needs 1 <= k <= 8 (returns cudaErrorInvalidValue
 // otherwise).
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
-                              __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s);
+                              __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s,
+                              float* out32 = nullptr, F16State* st = nullptr);
+// FP64 residual written as FP32 at pitch Px with its max |r| in state slot 0
+// (the F16X3 tier then splits it with launch_split_f16).  1 <= k <= 8.
+cudaError_t launch_stencil_f32out(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f,
+                                  float* out32, F16State* st, cudaStream_t s);
 // FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads.
 cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 
@@ -132,7 +164,14 @@ struct TcPassPlan;
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
-                                       DfBuffers df = DfBuffers{nullptr, nullptr}, int nprod = 3);
+                                       DfBuffers df = DfBuffers{nullptr, nullptr}, int nprod = 3,
+                                       const F16Pass* f16 = nullptr);
+// F16X3 split input: fp16 hi + lo of x * 2^e at pitch Px (zero pads), with e
+// chosen from state slot 0's max so the largest |x * 2^e| is near 2^15.
+// in is FP64 (pitch nx) or FP32 (pitch Px).
+cudaError_t launch_absmax_f64(const Geom& g, const double* in, F16State* st, cudaStream_t s);
+cudaError_t launch_split_f16(const Geom& g, const void* in, bool in_f64, __half* hi, __half* lo, F16State* st,
+                             cudaStream_t s);
 
 // ---- Cahn-Hilliard pointwise kernels (ch_kernels.cu)
 struct ChParams {

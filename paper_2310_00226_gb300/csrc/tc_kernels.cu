@@ -156,11 +156,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
-// B bf16 (bits 7-9 = 1, 10-12 = 1), A major-ness at bit 15 (1 = MN-major),
+// B format at bits 7-9 and 10-12 (0 = fp16, 1 = bf16; both operands of one
+// MMA always share the format), A major-ness at bit 15 (1 = MN-major),
 // B K-major, N>>3 at bits 17-22, M>>4 at bits 24-28.
-__host__ __device__ constexpr uint32_t make_idesc(int m, int n, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
+__host__ __device__ constexpr uint32_t make_idesc(int m, int n, bool a_mn_major, int fmt) {
+  return (1u << 4) | ((fmt == 1 ? 0u : 1u) << 7) | ((fmt == 1 ? 0u : 1u) << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -214,6 +215,11 @@ struct TcArgs {
   const float *lamx, *lamy, *lamz;
   float c;
   int* err;
+  // F16X3 scaling (FMT = 1): state slots read / written, W scale exponent,
+  // infinity norm of W and the division bound (see F16Pass).
+  F16State* st;
+  int pin, pout, eW;
+  float normW, div_bound;
 };
 
 // Output modes of the epilogue.  The DF modes (y and z passes only) keep the
@@ -233,6 +239,30 @@ __device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uin
   const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(v1 - h1), "f"(v0 - h0));
 }
+
+// Split two FP32 values into fp16 hi + lo pairs (packed f16x2, element 0 in
+// the low half): hi = rn(v), lo = rn(v - hi).
+__device__ __forceinline__ void split_pair_f16(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(v1), "f"(v0));
+  const float h0 = __half2float(__ushort_as_half((unsigned short)(hi & 0xFFFFu)));
+  const float h1 = __half2float(__ushort_as_half((unsigned short)(hi >> 16)));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(v1 - h1), "f"(v0 - h0));
+}
+
+template <int FMT>
+__device__ __forceinline__ void split_any(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  if (FMT == 1) split_pair_f16(v0, v1, hi, lo);
+  else split_pair(v0, v1, hi, lo);
+}
+
+// Scale 2^e that maps a bound B of |values| to at most 2^15 (fp16 max 65504).
+__device__ __forceinline__ int f16_exponent(float bound) {
+  if (!(bound > 0.f) || !isfinite(bound)) return 0;
+  int e = ilogbf(32768.f / bound);
+  return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 
 // Exact FP32 -> FP64 conversion with integer operations (keeps the FP64 pipe,
 // ~1/64 of the FP32 rate on this GPU, free for the update's addition).
@@ -257,9 +287,16 @@ __device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
 //   so each thread writes 16-byte vectors of its own line.
 // y / z passes: row = contiguous index (i, or i + Px*j), the output axis has
 //   a stride, and the 32 lanes of a warp write 32 consecutive elements.
-template <int PASS, int MODE, int NP>
-__device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32]) {
+// sc_in: accumulator -> true value (2^-(e_in + eW), 1 for bf16); sc_out: true
+// value -> stored split value (2^e_out, 1 for bf16); vmax: running max |true|.
+template <int PASS, int MODE, int NP, int FMT>
+__device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32],
+                                               float sc_in, float sc_out, float& vmax) {
   const bool full = col0 + 32 <= a.nout;
+  if (FMT == 1) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] *= sc_in;
+  }
   if (PASS == 0) {
     if (row >= a.rows) return;
     if (MODE == OUT_DIV_SPLIT) {
@@ -270,6 +307,13 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
         const int o = col0 + q;
         const float d = (full || o < a.nout) ? __ldg(a.lamx + o) + s : 1.0f;
         v[q] = __fdividef(v[q], d);
+      }
+    }
+    if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        if (full || col0 + q < a.nout) vmax = fmaxf(vmax, fabsf(v[q]));
+        v[q] *= sc_out;
       }
     }
     if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
@@ -294,10 +338,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
       for (int g = 0; g < 4; ++g) {
         if (col0 + 8 * g + 8 > a.Px) break;  // Px is a multiple of 16
         uint4 hh, ll;
-        split_pair(v[8 * g + 0], v[8 * g + 1], hh.x, ll.x);
-        split_pair(v[8 * g + 2], v[8 * g + 3], hh.y, ll.y);
-        split_pair(v[8 * g + 4], v[8 * g + 5], hh.z, ll.z);
-        split_pair(v[8 * g + 6], v[8 * g + 7], hh.w, ll.w);
+        split_any<FMT>(v[8 * g + 0], v[8 * g + 1], hh.x, ll.x);
+        split_any<FMT>(v[8 * g + 2], v[8 * g + 3], hh.y, ll.y);
+        split_any<FMT>(v[8 * g + 4], v[8 * g + 5], hh.z, ll.z);
+        split_any<FMT>(v[8 * g + 6], v[8 * g + 7], hh.w, ll.w);
         *reinterpret_cast<uint4*>(dh + 8 * g) = hh;
         if (NP == 3) *reinterpret_cast<uint4*>(dl + 8 * g) = ll;
       }
@@ -326,6 +370,13 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
       const int o = col0 + q;
       const float d = (full || o < a.nout) ? li + fixed + __ldg(lv + o) : 1.0f;
       v[q] = __fdividef(v[q], d);
+    }
+  }
+  if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      if (full || col0 + q < a.nout) vmax = fmaxf(vmax, fabsf(v[q]));
+      v[q] *= sc_out;
     }
   }
   if (MODE == OUT_DF_STORE || MODE == OUT_DF_ACCUM || MODE == OUT_DF_ACCUM_F64) {
@@ -390,7 +441,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
 #pragma unroll
     for (int q = 0; q < 32; q += 2) {
       uint32_t hh, ll;
-      split_pair(v[q], v[q + 1], hh, ll);
+      split_any<FMT>(v[q], v[q + 1], hh, ll);
       if (full || col0 + q < a.nout) { st_b16(ph, hh); if (NP == 3) st_b16(pl, ll); }
       ph += cs; pl += cs;
       if (full || col0 + q + 1 < a.nout) { st_b16(ph, hh >> 16); if (NP == 3) st_b16(pl, ll >> 16); }
@@ -408,7 +459,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
 // arrives on the "empty" barrier of all CL CTAs (count CL).
 // NP = 3: BF16x3 (A_hi W_hi + A_hi W_lo + A_lo W_hi); NP = 1: single bf16
 // product A_hi W_hi (the lo arrays are neither loaded nor written).
-template <int PASS, int MODE, int CL, int NP>
+template <int PASS, int MODE, int CL, int NP, int FMT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -513,7 +564,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer
-    constexpr uint32_t idesc = make_idesc(BM, BN, a_mn);
+    constexpr uint32_t idesc = make_idesc(BM, BN, a_mn, FMT);
     // K-major tiles (rows of BK = 32 bf16 = 64 B, 64-byte swizzle): SBO 512
     //   (next 8-row group), advance 32 B per K = 16 inside the swizzled row.
     // MN-major A (64 rows = 128 B per K row, 128-byte swizzle): LBO 4096 (next
@@ -565,6 +616,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int quad = warp & 3;
     const int slice = (warp - 2) >> 2;
     constexpr int COLS = BN / (EPI_WARPS / 4);
+    // F16X3: scales from the state the previous kernels left (every CTA
+    // computes the same values; one thread publishes this pass's exponent).
+    float sc_in = 1.f, sc_out = 1.f;
+    if (FMT == 1) {
+      const int e_in = a.st->e[a.pin];
+      const float max_in = __uint_as_float(a.st->maxbits[a.pin]);
+      sc_in = exp2i(-(e_in + a.eW));
+      const int e_out = f16_exponent(a.normW * max_in * a.div_bound);
+      sc_out = exp2i(e_out);
+      if (blockIdx.x == 0 && warp == 2 && lane == 0) a.st->e[a.pout] = e_out;
+    }
+    float vmax = 0.f;
     int tl = 0;
     for (int ct = cid; ct < total_ct; ct += ncl, ++tl) {
       const int buf = tl & 1;
@@ -583,11 +646,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
         float v[32];
         tmem_ld32(taddr + ch * 32, v);
-        epilogue_chunk<PASS, MODE, NP>(a, row, col0, b, v);
+        epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(buf));
+    }
+    if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
+      if (lane == 0 && vmax > 0.f) atomicMax(&a.st->maxbits[a.pout], __float_as_uint(vmax));
     }
   }
   __syncwarp();
@@ -640,10 +708,10 @@ namespace {
 #endif
 constexpr int CLUSTER = SEM3D_TC_CLUSTER;
 
-template <int PASS, int MODE, int NP>
+template <int PASS, int MODE, int NP, int FMT = 0>
 cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                       const TcArgs& a, long long work_clusters, int num_sms, cudaStream_t s) {
-  auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER, NP>;
+  auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER, NP, FMT>;
   static int max_clusters = 0;  // per instantiation: co-resident clusters of CLUSTER CTAs
   if (max_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -686,8 +754,24 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
 }
 
 template <int PASS>
-cudaError_t launch_tc_mode(int mode, int nprod, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
-                           const CUtensorMap& b1, const TcArgs& a, long long work, int num_sms, cudaStream_t s) {
+cudaError_t launch_tc_mode(int mode, int nprod, int fmt, const CUtensorMap& a0, const CUtensorMap& a1,
+                           const CUtensorMap& b0, const CUtensorMap& b1, const TcArgs& a, long long work, int num_sms,
+                           cudaStream_t s) {
+  if (fmt == 1) {
+    switch (mode) {
+      case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      case OUT_DIV_SPLIT: return launch_tc<PASS, OUT_DIV_SPLIT, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      case OUT_F64: return launch_tc<PASS, OUT_F64, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      case OUT_F64_ACCUM: return launch_tc<PASS, OUT_F64_ACCUM, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+      default:
+        if constexpr (PASS == 2) {
+          if (mode == OUT_DF_STORE) return launch_tc<PASS, OUT_DF_STORE, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+          if (mode == OUT_DF_ACCUM) return launch_tc<PASS, OUT_DF_ACCUM, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+          return launch_tc<PASS, OUT_DF_ACCUM_F64, 3, 1>(a0, a1, b0, b1, a, work, num_sms, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+  }
   if (nprod == 1) {
     switch (mode) {
       case OUT_SPLIT: return launch_tc<PASS, OUT_SPLIT, 1>(a0, a1, b0, b1, a, work, num_sms, s);
@@ -722,8 +806,10 @@ static constexpr CUtensorMapSwizzle SWZ_MN = CU_TENSOR_MAP_SWIZZLE_128B;
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
-                                       DfBuffers df, int nprod) {
+                                       DfBuffers df, int nprod, const F16Pass* f16) {
   if (nprod != 1 && nprod != 3) return cudaErrorInvalidValue;
+  const int fmt = f16 ? 1 : 0;
+  if (fmt == 1 && nprod != 3) return cudaErrorInvalidValue;
   int mode;
   if (epi == EPI_DF_STORE || epi == EPI_DF_ACCUM || epi == EPI_DF_ACCUM_F64) {
     if (axis != 2 || !df.hi || !df.lo || (epi == EPI_DF_ACCUM_F64 && !out64)) return cudaErrorInvalidValue;
@@ -737,6 +823,14 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   TcArgs a{};
   a.df_hi = df.hi;
   a.df_lo = df.lo;
+  if (f16) {
+    a.st = f16->st;
+    a.pin = f16->pin;
+    a.pout = f16->pout;
+    a.eW = W.eW16[which];
+    a.normW = W.normW[which];
+    a.div_bound = f16->div_bound;
+  }
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
   a.out_hi = out.hi; a.out_lo = out.lo; a.out64 = out64;
   a.lamx = lamx; a.lamy = lamy; a.lamz = lamz; a.c = (float)g.c;
@@ -772,8 +866,9 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
     const uint64_t dims[2] = {(uint64_t)W.n, (uint64_t)W.n};
     const uint64_t str[1] = {(uint64_t)W.Kp * 2};
     const uint32_t box[2] = {BK, (uint32_t)(BN / CLUSTER)};
-    ok = ok && make_map(&mBh, W.W_hi[which], 2, dims, str, box, SWZ_K) &&
-         make_map(&mBl, W.W_lo[which], 2, dims, str, box, SWZ_K);
+    const void* wh = fmt ? (const void*)W.W16_hi[which] : (const void*)W.W_hi[which];
+    const void* wl = fmt ? (const void*)W.W16_lo[which] : (const void*)W.W_lo[which];
+    ok = ok && make_map(&mBh, wh, 2, dims, str, box, SWZ_K) && make_map(&mBl, wl, 2, dims, str, box, SWZ_K);
   }
   if (!ok) return cudaErrorInvalidValue;
   a.nout = W.n;
@@ -782,9 +877,9 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   a.k_blocks = (nin + BK - 1) / BK;
   const long long work = (long long)((a.m_tiles + CLUSTER - 1) / CLUSTER) * a.n_tiles * a.batches;
   if (work >= (1LL << 31)) return cudaErrorInvalidValue;
-  if (axis == 0) return launch_tc_mode<0>(mode, nprod, mAh, mAl, mBh, mBl, a, work, num_sms, s);
-  if (axis == 1) return launch_tc_mode<1>(mode, nprod, mAh, mAl, mBh, mBl, a, work, num_sms, s);
-  return launch_tc_mode<2>(mode, nprod, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  if (axis == 0) return launch_tc_mode<0>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  if (axis == 1) return launch_tc_mode<1>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  return launch_tc_mode<2>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);
 }
 
 }  // namespace sem3d

@@ -168,6 +168,27 @@ def test_bf16_single_product_tier(sem3d, i):
     assert e8 < 1e-6 and e8 < 1e-3 * e0
 
 
+@pytest.mark.parametrize("i", [0, 1, 2, 3, 4, 5, 6])
+def test_f16x3_tier_matches_oracle(sem3d, i):
+    # fp16 hi + lo operands with device-chosen power-of-two scales: bare error
+    # well below BF16x3's, two sweeps (mixed residuals) reach rounding level.
+    n3, k, L3, c, (sx, sy, sz), F = _case(i)
+    ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.set_precision("f16x3", 0)
+        p.solve(f, u)
+        p.sync_check()
+        bare = _rel(u.cpu().numpy(), ref)
+        p.set_precision("f16x3", 2)
+        p.solve(f, u)
+        p.sync_check()
+        refined = _rel(u.cpu().numpy(), ref)
+    assert bare < 2e-5, bare
+    assert refined < 1e-12, refined
+
+
 def test_bf16x3_high_degree_falls_back_to_fp64_residuals(sem3d):
     # k = 10 > 8: the double-FP32 stencil is not instantiated; every sweep is FP64.
     n3, k, L3, c = (19, 29, 9), 10, (1.0, 1.0, 1.0), 1.0
