@@ -22,6 +22,7 @@ from .sem import (  # noqa: F401
     Sem1D,
     mode_product,
     fast_solve,
+    fast_solve_x_line,
     apply_h,
     apply_weak,
     refined_solve,

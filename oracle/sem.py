@@ -237,6 +237,28 @@ def fast_solve(F: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Sem1D, c: float) -> np.n
     return np.ascontiguousarray(U.T)
 
 
+def fast_solve_x_line(fx, fy, fz, sx: Sem1D, sy: Sem1D, sz: Sem1D, c: float, j: int, l: int) -> np.ndarray:
+    """Nodal values u[l, j, :] of ``fast_solve`` for a rank-one right-hand side
+    F[l, j, i] = fz[l] fy[j] fx[i], computed one x-line at a time so that it
+    can be evaluated on grids far too large for the whole field.
+
+    Eq. 13 for a separable F: T^{-1} acts on each factor alone
+    (xh = T_x^{-1} fx, ...), the division by lambda_x,a + lambda_y,b +
+    lambda_z,g + c couples the three spectral indices, and the backward
+    products give
+      u[l, j, i] = sum_a T_x[i, a] xh_a W_a,
+      W_a = sum_{b, g} T_y[j, b] yh_b T_z[l, g] zh_g
+                       / (lambda_x,a + lambda_y,b + lambda_z,g + c).
+    Cost n_y n_z per spectral x-index: n^3 for the line."""
+    xh = sx.Tinv @ np.asarray(fx, dtype=np.float64)
+    yh = sy.Tinv @ np.asarray(fy, dtype=np.float64)
+    zh = sz.Tinv @ np.asarray(fz, dtype=np.float64)
+    P = (sz.T[l, :] * zh)[:, None] * (sy.T[j, :] * yh)[None, :]   # (g, b)
+    lam_zy = sz.lam[:, None] + sy.lam[None, :] + c
+    W = np.array([np.sum(P / (lam_zy + la)) for la in sx.lam])
+    return sx.T @ (xh * W)
+
+
 def apply_h(Ug: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Sem1D, c: float) -> np.ndarray:
     """(c I + I(x)I(x)H_x + I(x)H_y(x)I + H_z(x)I(x)I) vec(U)  (Eq. 12 with
     H = M^{-1} S; the alpha term of Eq. 1 added as c).  Uses sparse H."""

@@ -170,6 +170,44 @@ def test_fast_solve_matches_dense_lu(case):
         assert np.abs(u - u_ref).max() / np.abs(u_ref).max() < 1e-11
 
 
+@pytest.mark.parametrize("case", range(3))
+def test_fast_solve_x_line_matches_dense_lu(case):
+    # Every x-line of the rank-one formula against the dense LU solve of the
+    # assembled system (non-cubic boxes, mixed degrees).
+    from oracle import fast_solve_x_line
+    (bx, by, bz, c, bc) = _boxes()[case]
+    sx = sem_1d(bx[0], bx[1], 0.0, bx[2], bc)
+    sy = sem_1d(by[0], by[1], 0.0, by[2], bc)
+    sz = sem_1d(bz[0], bz[1], 0.0, bz[2], bc)
+    rng = np.random.Generator(np.random.PCG64(40 + case))
+    fx, fy, fz = rng.standard_normal(sx.n), rng.standard_normal(sy.n), rng.standard_normal(sz.n)
+    F = fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    u_ref = dense_solve(F, sx, sy, sz, c)
+    scale = np.abs(u_ref).max()
+    for l in range(sz.n):
+        for j in range(sy.n):
+            line = fast_solve_x_line(fx, fy, fz, sx, sy, sz, c, j, l)
+            assert np.abs(line - u_ref[l, j]).max() / scale < 1e-12
+
+
+def test_fast_solve_x_line_manufactured_q4():
+    # u = e^x sin(pi x) sin(pi y) sin(pi z) has a rank-one right-hand side;
+    # at Q^4, Ne = 16 the discrete solution is within 3e-10 of it (order k+2).
+    from oracle import fast_solve_x_line
+    from paper_2310_00226_gb300.inputs import exp_sine
+    s = sem_1d(4, 16, 0.0, 1.0)
+    c = 1.0
+    fx = np.exp(s.x) * ((3 * np.pi**2 - 1 + c) * np.sin(np.pi * s.x) - 2 * np.pi * np.cos(np.pi * s.x))
+    g = np.sin(np.pi * s.x)
+    u_ex, F = exp_sine(s.x, s.x, s.x, c)
+    assert np.abs(F - g[:, None, None] * g[None, :, None] * fx[None, None, :]).max() < 1e-12 * np.abs(F).max()
+    U = fast_solve(F, s, s, s, c)
+    for (j, l) in ((0, 0), (31, 17), (62, 40)):
+        line = fast_solve_x_line(fx, g, g, s, s, s, c, j, l)
+        assert np.abs(line - U[l, j]).max() < 1e-13
+        assert np.abs(line - u_ex[l, j]).max() < 3e-10
+
+
 def test_operators_match_kronecker_assembly():
     sx, sy, sz = sem_1d(2, 3, 0.0, 1.0), sem_1d(3, 2, 0.0, 0.8), sem_1d(4, 2, 0.0, 1.2)
     c = 0.75
