@@ -9,7 +9,13 @@ CUDA path:
 * every node against a manufactured solution, where the oracle's convergence
   (order k+2, measured here on small grids) puts the discretisation error far
   below the tolerance, so the manufactured solution IS the discrete solution
-  to that accuracy;
+  to that accuracy.  What remains is the FP64 floor of the discrete problem:
+  the oracle's own refined solve sits 1.2e-12 (n=255) and 4.6e-12 (n=511)
+  from it, and perturbing the 1D operator's entries by one ulp moves the
+  oracle's solution by 1.3e-13 (n=127) and 5e-13 (n=255), growing with the
+  condition number (~n^2): ~8e-12 at n=999.  So at n=999 the bound is 1e-11;
+  the 1e-12 element-by-element parity is tested where the oracle solves the
+  whole field (test_gpu_parity.py, up to n=383);
 * the componentwise backward error on sampled lines, from the oracle's S and M:
       eta = max_i |b - A u|_i / (|A| |u| + |b|)_i ,
   the relative change of the data that makes u exact.  A solve refined to FP64
@@ -146,11 +152,11 @@ def q4_n999(sem3d):
     _free()
 
 
-# (tier, sweeps, residual mode, tolerance vs the discrete solution, backward-error bound)
+# (tier, sweeps, residual mode, tolerance vs the manufactured solution, backward-error bound)
 HEADLINE = [
-    ("bf16x3", 3, "mixed", 1e-12, 1e-14),   # the timed fast path
-    ("bf16x3", 3, "fp64", 1e-12, 1e-14),
-    ("fp64", 1, "fp64", 1e-12, 1e-14),      # the timed plain path
+    ("bf16x3", 3, "mixed", 1e-11, 1e-14),   # the timed fast path
+    ("bf16x3", 3, "fp64", 1e-11, 1e-14),
+    ("fp64", 1, "fp64", 1e-11, 1e-14),      # the timed plain path
     ("fp32", 0, "mixed", 1e-5, None),       # unrefined FP32 (spec bound 1e-5)
     ("bf16x3", 0, "mixed", 5e-4, None),     # unrefined BF16x3 (measured 4.3e-5)
 ]
