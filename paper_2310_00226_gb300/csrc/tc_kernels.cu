@@ -200,10 +200,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
+      "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
+      "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
+      "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
+      "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ---------------------------------------------------------------- kernel
 
 struct TcArgs {
   int m_tiles, n_tiles, batches, k_blocks;
+  int kc;              // K blocks per TMEM accumulation chunk (see the kernel)
   int rows;            // valid tile rows per batch (x: ny*nz, y: Px, z: Px*ny)
   int nout;            // valid outputs (length of the output axis)
   int nx, ny, nz, Px;
@@ -459,6 +479,16 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
 // arrives on the "empty" barrier of all CL CTAs (count CL).
 // NP = 3: BF16x3 (A_hi W_hi + A_hi W_lo + A_lo W_hi); NP = 1: single bf16
 // product A_hi W_hi (the lo arrays are neither loaded nor written).
+//
+// Accumulation chunks: the tensor core adds each MMA's products into its FP32
+// accumulator with an error of about 2^-24 of the accumulator per K = 16 step
+// that does not average out, so a K = 1000 contraction loses ~60 such steps.
+// The MMA warp therefore fills the two TMEM buffers in turn with partial sums
+// over a.kc K blocks each.  With FMT = 1 (fp16 hi/lo operands, whose own
+// rounding is ~2^-22) the epilogue adds the chunks with FP32 round-to-nearest
+// additions, so no tensor-core accumulation runs longer than a.kc * BK; with
+// bf16 operands (rounding ~2^-17, which dominates) a.kc covers the whole K and
+// each TMEM buffer holds one finished tile as before.
 template <int PASS, int MODE, int CL, int NP, int FMT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
@@ -572,39 +602,42 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     //   K = 16.
     constexpr uint32_t a_lbo = a_mn ? 4096u : 16u, a_sbo = a_mn ? 1024u : 512u, a_kstep = a_mn ? 2048u : 32u;
     constexpr uint32_t a_layout = a_mn ? LAYOUT_SW128 : LAYOUT_SW64;
-    int it = 0, tl = 0;
+    int it = 0, cc = 0;  // cc: accumulation chunks issued (TMEM buffer cc & 1)
     bool ok = true;
-    for (int ct = cid; ct < total_ct && ok; ct += ncl, ++tl) {
-      const int buf = tl & 1;
-      if (!mbar_wait(tempty_bar(buf), ((tl >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
-      tc_fence_after();
-      const uint32_t tmem_d = tmem_base + (uint32_t)(buf * BN);
-      for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
-        const int s = it % STAGES;
-        if (!mbar_wait(full_bar(s), (it / STAGES) & 1, a.err)) { ok = false; break; }
+    for (int ct = cid; ct < total_ct && ok; ct += ncl) {
+      for (int kb0 = 0; kb0 < a.k_blocks; kb0 += a.kc, ++cc) {
+        const int buf = cc & 1;
+        if (!mbar_wait(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
-        const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
+        const uint32_t tmem_d = tmem_base + (uint32_t)(buf * BN);
+        const int kb1 = kb0 + a.kc < a.k_blocks ? kb0 + a.kc : a.k_blocks;
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (!mbar_wait(full_bar(s), (it / STAGES) & 1, a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
+          const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
 #pragma unroll
-        for (int k16 = 0; k16 < BK / 16; ++k16) {
-          const uint64_t dah = smem_desc(a_hi + k16 * a_kstep, a_lbo, a_sbo, a_layout);
-          const uint64_t dal = smem_desc(a_lo + k16 * a_kstep, a_lbo, a_sbo, a_layout);
-          const uint64_t dbh = smem_desc(b_hi + k16 * 32u, 16u, 512u, LAYOUT_SW64);
-          const uint64_t dbl = smem_desc(b_lo + k16 * 32u, 16u, 512u, LAYOUT_SW64);
-          const uint32_t acc = (kb | k16) ? 1u : 0u;
-          mma_bf16(tmem_d, dah, dbh, idesc, acc);
-          if (NP == 3) {
-            mma_bf16(tmem_d, dah, dbl, idesc, 1u);
-            mma_bf16(tmem_d, dal, dbh, idesc, 1u);
+          for (int k16 = 0; k16 < BK / 16; ++k16) {
+            const uint64_t dah = smem_desc(a_hi + k16 * a_kstep, a_lbo, a_sbo, a_layout);
+            const uint64_t dal = smem_desc(a_lo + k16 * a_kstep, a_lbo, a_sbo, a_layout);
+            const uint64_t dbh = smem_desc(b_hi + k16 * 32u, 16u, 512u, LAYOUT_SW64);
+            const uint64_t dbl = smem_desc(b_lo + k16 * 32u, 16u, 512u, LAYOUT_SW64);
+            const uint32_t acc = ((kb - kb0) | k16) ? 1u : 0u;
+            mma_bf16(tmem_d, dah, dbh, idesc, acc);
+            if (NP == 3) {
+              mma_bf16(tmem_d, dah, dbl, idesc, 1u);
+              mma_bf16(tmem_d, dal, dbh, idesc, 1u);
+            }
           }
+          // The stage is free (in every CTA of the cluster) once these MMAs finish.
+          if (CL == 1) mma_commit(empty_bar(s));
+          else mma_commit_mc(empty_bar(s), kMask);
         }
-        // The stage is free (in every CTA of the cluster) once these MMAs finish.
-        if (CL == 1) mma_commit(empty_bar(s));
-        else mma_commit_mc(empty_bar(s), kMask);
+        if (!ok) break;
+        mma_commit(tfull_bar(buf));  // chunk ready for the epilogue
       }
-      if (!ok) break;
-      mma_commit(tfull_bar(buf));  // accumulator ready for the epilogue
     }
     // Drain: wait for every MMA this thread issued before TMEM is freed.
     mma_commit(drain_bar);
@@ -628,29 +661,71 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (blockIdx.x == 0 && warp == 2 && lane == 0) a.st->e[a.pout] = e_out;
     }
     float vmax = 0.f;
-    int tl = 0;
-    for (int ct = cid; ct < total_ct; ct += ncl, ++tl) {
-      const int buf = tl & 1;
-      if (!mbar_wait(tfull_bar(buf), (tl >> 1) & 1, a.err)) break;
-      tc_fence_after();
+    int cc = 0;
+    bool ok = true;
+    for (int ct = cid; ct < total_ct && ok; ct += ncl) {
       const int b = ct / tiles_per_batch;
       const int rem = ct - b * tiles_per_batch;
       const int mg = rem / a.n_tiles, nt = rem - mg * a.n_tiles;
       const int mt = mg * CL + rank;
       const int row = mt * BM + quad * 32 + lane;
-      const uint32_t taddr =
-          tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + slice * COLS);
+      const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slice * COLS);
+      if constexpr (FMT == 1) {
+        // Sum the tile's chunks with round-to-nearest FP32 additions.  The
+        // running sum moves with the chunks: consuming chunk c adds the sum so
+        // far (in the previous chunk's buffer) into chunk c's buffer and
+        // releases the previous one, so the MMA always has a buffer to fill.
+        int prev = -1;
+        for (int kb0 = 0; kb0 < a.k_blocks; kb0 += a.kc, ++cc) {
+          const int buf = cc & 1;
+          if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err)) { ok = false; break; }
+          tc_fence_after();
+          if (prev >= 0) {
 #pragma unroll 1
-      for (int ch = 0; ch < COLS / 32; ++ch) {
-        const int col0 = nt * BN + slice * COLS + ch * 32;
-        if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
-        float v[32];
-        tmem_ld32(taddr + ch * 32, v);
-        epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax);
+            for (int g = 0; g < COLS / 32; ++g) {
+              float x[32], y[32];
+              tmem_ld32(lane_addr + (uint32_t)(buf * BN + g * 32), x);
+              tmem_ld32(lane_addr + (uint32_t)(prev * BN + g * 32), y);
+#pragma unroll
+              for (int q = 0; q < 32; ++q) x[q] += y[q];
+              tmem_st32(lane_addr + (uint32_t)(buf * BN + g * 32), x);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(prev));
+          }
+          prev = buf;
+        }
+        if (!ok) break;
+#pragma unroll 1
+        for (int ch = 0; ch < COLS / 32; ++ch) {
+          const int col0 = nt * BN + slice * COLS + ch * 32;
+          if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(prev * BN + ch * 32), v);
+          epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(prev));
+      } else {
+        const int c = cc++;  // one chunk per tile (a.kc >= a.k_blocks)
+        const int buf = c & 1;
+        if (!mbar_wait(tfull_bar(buf), (c >> 1) & 1, a.err)) break;
+        tc_fence_after();
+#pragma unroll 1
+        for (int ch = 0; ch < COLS / 32; ++ch) {
+          const int col0 = nt * BN + slice * COLS + ch * 32;
+          if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(buf * BN + ch * 32), v);
+          epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(buf));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(buf));
     }
     if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
 #pragma unroll
@@ -707,6 +782,11 @@ namespace {
 #define SEM3D_TC_CLUSTER 4
 #endif
 constexpr int CLUSTER = SEM3D_TC_CLUSTER;
+
+// K blocks (of BK) per tensor-core accumulation chunk with fp16 hi/lo operands.
+#ifndef SEM3D_TC_CHUNK_KBLOCKS
+#define SEM3D_TC_CHUNK_KBLOCKS 8
+#endif
 
 template <int PASS, int MODE, int NP, int FMT = 0>
 cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
@@ -875,6 +955,7 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   a.m_tiles = (a.rows + BM - 1) / BM;
   a.n_tiles = (W.n + BN - 1) / BN;
   a.k_blocks = (nin + BK - 1) / BK;
+  a.kc = (fmt == 1 && SEM3D_TC_CHUNK_KBLOCKS > 0) ? SEM3D_TC_CHUNK_KBLOCKS : a.k_blocks;
   const long long work = (long long)((a.m_tiles + CLUSTER - 1) / CLUSTER) * a.n_tiles * a.batches;
   if (work >= (1LL << 31)) return cudaErrorInvalidValue;
   if (axis == 0) return launch_tc_mode<0>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);

@@ -16,11 +16,18 @@ CUDA path:
   condition number (~n^2): ~8e-12 at n=999.  So at n=999 the bound is 1e-11;
   the 1e-12 element-by-element parity is tested where the oracle solves the
   whole field (test_gpu_parity.py, up to n=383);
-* the componentwise backward error on sampled lines, from the oracle's S and M:
-      eta = max_i |b - A u|_i / (|A| |u| + |b|)_i ,
-  the relative change of the data that makes u exact.  A solve refined to FP64
-  has eta of a few 1e-16; a bare FP64 fast solve a few 1e-14; a relative
-  perturbation of u by 1e-13 already gives ~2e-13 (measured with the oracle).
+* backward errors on sampled lines, from the oracle's S and M (the relative
+  change of the data that makes u exact):
+      componentwise  eta_c = max_i |b - A u|_i / (|A| |u| + |b|)_i ,
+      normwise       eta_n = max_i |b - A u|_i / (||A|| ||u|| + ||b||)  (inf-norms).
+  Measured with the oracle: a solve refined in FP64 has eta_c of a few 1e-16
+  and eta_n ~4e-17; a bare FP64 fast solve eta_c of a few 1e-14 and eta_n
+  ~6e-16; random noise of 1e-16 max|u| added to the refined solve gives eta_n
+  1.2e-16.  eta_c needs errors proportional to the local |u|, which FP64
+  arithmetic gives; the tensor-core tiers' corrections carry errors relative
+  to max|u| (their mode products mix the whole line), and where u is ~1e-5 of
+  its maximum (the corner lines of the manufactured solution) eta_c reads a
+  1e-16 absolute error as ~1e-11.  Those tiers are held to eta_n.
 
 Tolerances are stated per check below.  Every test here allocates tens of GB
 on the device and runs minutes of host-side oracle work: marked ``slow``.
@@ -87,6 +94,26 @@ def _kron_lines(B, l0, j0, pairs, Ax, Ay, Az, Mx, My, Mz):
     return out
 
 
+def _norm_inf_weak(sx, sy, sz, c):
+    """||S(+)S(+)S + c M3||_inf: the largest row sum of |A|, one z-plane at a time."""
+    rx, ry, rz = (np.abs(s.S).sum(1) for s in (sx, sy, sz))
+    plane = rx[None, :] * sy.M[:, None] + sx.M[None, :] * ry[:, None] + c * sx.M[None, :] * sy.M[:, None]
+    mm = sx.M[None, :] * sy.M[:, None]
+    return float(max((sz.M[l] * plane + rz[l] * mm).max() for l in range(sz.n)))
+
+
+def _normwise_backward_error(u_dev, f_dev, sx, sy, sz, c, pairs, k, a_inf, b_inf):
+    """max over the sampled lines of |b - A u| / (||A|| ||u|| + ||b||)."""
+    rmax = 0.0
+    for (j, l) in pairs:
+        B, l0, j0 = _block(u_dev, l, j, k)
+        m3 = sz.M[l] * sy.M[j] * sx.M
+        Au = _kron_lines(B, l0, j0, [(l, j)], sx.S, sy.S, sz.S, sx.M, sy.M, sz.M)[0]
+        r = m3 * f_dev[l, j].cpu().numpy() - Au - m3 * c * B[l - l0, j - j0]
+        rmax = max(rmax, float(np.abs(r).max()))
+    return rmax / (a_inf * float(u_dev.abs().max()) + b_inf)
+
+
 def _backward_error(u_dev, f_dev, sx, sy, sz, shift, pairs, k):
     """max over the sampled lines of |b - A u| / (|A| |u| + |b|) for the weak
     form A = S(+)S(+)S + M3 diag(shift), b = M3 f (Eq. 12 with the alpha term)."""
@@ -141,30 +168,33 @@ def q4_n999(sem3d):
     n = s.n
     plan = sem3d.Plan(n, n, n, K4, (1.0, 1.0, 1.0), C4)
     np.testing.assert_allclose(plan.nodes(0), s.x, atol=1e-15)
+    b_inf = float(max(np.abs(F[l] * (s.M[l] * s.M[:, None] * s.M[None, :])).max() for l in range(n)))
+    a_inf = _norm_inf_weak(s, s, s, C4)
     f = torch.from_numpy(F).cuda()
     del F
     uex = torch.from_numpy(u_ex).cuda()
     del u_ex
     u = torch.empty_like(f)
-    yield s, plan, f, uex, u
+    yield s, plan, f, uex, u, a_inf, b_inf
     plan.close()
     del f, uex, u
     _free()
 
 
-# (tier, sweeps, residual mode, tolerance vs the manufactured solution, backward-error bound)
+# (tier, sweeps, residual mode, tolerance vs the manufactured solution,
+#  normwise backward-error bound, componentwise backward-error bound)
 HEADLINE = [
-    ("bf16x3", 3, "mixed", 1e-11, 1e-14),   # the timed fast path
-    ("bf16x3", 3, "fp64", 1e-11, 1e-14),
-    ("fp64", 1, "fp64", 1e-11, 1e-14),      # the timed plain path
-    ("fp32", 0, "mixed", 1e-5, None),       # unrefined FP32 (spec bound 1e-5)
-    ("bf16x3", 0, "mixed", 5e-4, None),     # unrefined BF16x3 (measured 4.3e-5)
+    ("bf16x3", 3, "mixed", 1e-11, 3e-16, None),   # the timed fast path
+    ("bf16x3", 3, "fp64", 1e-11, 3e-16, None),
+    ("fp64", 1, "fp64", 1e-11, 3e-16, 1e-14),     # the timed plain path
+    ("fp32", 0, "mixed", 1e-5, None, None),       # unrefined FP32 (spec bound 1e-5)
+    ("bf16x3", 0, "mixed", 5e-4, None, None),     # unrefined BF16x3 (measured 4.3e-5)
 ]
 
 
-@pytest.mark.parametrize("tier,sweeps,residual,tol,eta_max", HEADLINE)
-def test_q4_n999_solve(q4_n999, tier, sweeps, residual, tol, eta_max):
-    s, plan, f, uex, u = q4_n999
+@pytest.mark.parametrize("tier,sweeps,residual,tol,eta_n_max,eta_c_max", HEADLINE)
+def test_q4_n999_solve(q4_n999, tier, sweeps, residual, tol, eta_n_max, eta_c_max):
+    s, plan, f, uex, u, a_inf, b_inf = q4_n999
     plan.set_precision(tier, sweeps)
     plan.set_residual(residual)
     u.fill_(float("nan"))
@@ -173,10 +203,14 @@ def test_q4_n999_solve(q4_n999, tier, sweeps, residual, tol, eta_max):
     umax = float(uex.abs().max())
     err = float((u - uex).abs().max()) / umax
     assert err < tol, err
-    if eta_max is None:
+    if eta_n_max is None:
         return
-    eta = _backward_error(u, f, s, s, s, C4, _lines(s.n, s.n, 3, seed=7), K4)
-    assert eta < eta_max, eta
+    pairs = _lines(s.n, s.n, 3, seed=7)
+    eta_n = _normwise_backward_error(u, f, s, s, s, C4, pairs, K4, a_inf, b_inf)
+    assert eta_n < eta_n_max, eta_n
+    if eta_c_max is not None:
+        eta_c = _backward_error(u, f, s, s, s, C4, pairs, K4)
+        assert eta_c < eta_c_max, eta_c
     # Two x-lines against the oracle evaluated line by line.  The oracle's own
     # FP64 eigenvectors carry the low modes to about eps * lambda_max / lambda_1
     # = 1.3e-10 (lambda_max = 1.15e7, lambda_1 = pi^2): that, not the GPU path,
