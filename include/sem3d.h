@@ -238,6 +238,22 @@ sem3d_status sem3d_sync_check(sem3d_handle h, void* stream);
 sem3d_status sem3d_profile(sem3d_handle h, int enable);
 sem3d_status sem3d_profile_read(sem3d_handle h, int kind, long long* launches, double* total_ms);
 
+/* The FP32 mode-product configuration the autotuner chose for this plan's
+ * pass along `axis` (0 = x, 1 = y, 2 = z).  sem3d_set_precision(h, SEM3D_FP32,
+ * ...) measures six configurations of the FP32 CUDA-core kernel on each pass
+ * shape of the plan that the process has not measured before (synchronous;
+ * scratch buffers of up to 65536 * n floats twice) and keeps the fastest:
+ *   0 = 128 x 128 output tile, 8 x 8 per thread, two shared-memory stages,
+ *   1 = 128 x 64, 8 x 4, two stages,   2 = 64 x 64, 4 x 4, two stages,
+ *   3..5 = the same three tiles with one stage.
+ * Shapes never measured report 0 (the default).  The grouped launch of
+ * sem3d_solve_batched uses the two-stage tile of the same shape. */
+sem3d_status sem3d_tuned_config(sem3d_handle h, int axis, int* config);
+/* Pin `config` (0..5) for the pass shape of this plan's `axis`, replacing the
+ * measured choice for every plan of the process with that pass shape (until
+ * the next pin; sem3d_set_precision does not re-measure a known shape). */
+sem3d_status sem3d_set_tuned_config(sem3d_handle h, int axis, int config);
+
 /* Total number of kernels this plan has launched since sem3d_setup. */
 sem3d_status sem3d_launch_count(sem3d_handle h, unsigned long long* count);
 

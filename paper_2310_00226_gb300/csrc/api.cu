@@ -386,8 +386,27 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweep
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
     if (major != 10 || minor != 3) return fail(SEM3D_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 GPU");
   }
+  if (prec == SEM3D_FP32) {
+    const cudaError_t e = f32_autotune(h->g, h->dev);
+    if (e != cudaSuccess) return fail(SEM3D_ERR_CUDA, std::string("FP32 autotuning: ") + cudaGetErrorString(e));
+  }
   h->prec = prec;
   h->sweeps = sweeps;
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_set_tuned_config(sem3d_handle h, int axis, int config) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  if (axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
+  if (config < 0 || config > 5) return fail(SEM3D_ERR_INVALID_ARG, "config must be in [0, 5]");
+  f32_set_config(axis, h->g, config);
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_tuned_config(sem3d_handle h, int axis, int* config) {
+  if (!h || !config) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  if (axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
+  *config = f32_config(axis, h->g);
   return SEM3D_OK;
 }
 

@@ -124,6 +124,12 @@ cudaError_t launch_mode_product_f64(const Geom& g, int axis, const double* W, co
 cudaError_t launch_mode_product_f32(const Geom& g, int axis, const float* W, const void* in, bool in_f64, void* out,
                                     bool out_f64, int epi, const double* lamx, const double* lamy, const double* lamz,
                                     cudaStream_t s);
+// Measure the FP32 kernel configurations on the three pass shapes of grid g
+// (once per shape per process; synchronous) and record the fastest; later
+// launches of those shapes use it.  f32_config reports the choice for an axis.
+cudaError_t f32_autotune(const Geom& g, const DevAxis* ax);
+int f32_config(int axis, const Geom& g);
+void f32_set_config(int axis, const Geom& g, int cfg);  // pin a configuration
 // The same pass for `count` independent problems in one grouped launch.
 // The per-problem descriptor table (count * ~160 B) is staged through
 // host_table (pinned, >= table_bytes) into dev_table with an async copy on s.

@@ -42,6 +42,8 @@ EXPORTS = (
     "sem3d_profile",
     "sem3d_profile_read",
     "sem3d_launch_count",
+    "sem3d_tuned_config",
+    "sem3d_set_tuned_config",
     "sem3d_solve_fp64_static",
     "sem3d_destroy",
     "sem3d_last_error",
@@ -88,6 +90,8 @@ def lib() -> ctypes.CDLL:
     L.sem3d_profile_read.argtypes = [c_void_p, c_int, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_double)]
     L.sem3d_launch_count.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.sem3d_tuned_config.argtypes = [c_void_p, c_int, ctypes.POINTER(c_int)]
+    L.sem3d_set_tuned_config.argtypes = [c_void_p, c_int, c_int]
     L.sem3d_solve_fp64_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_destroy.argtypes = [c_void_p]
     L.sem3d_last_error.restype = ctypes.c_char_p
@@ -226,6 +230,16 @@ class Plan:
         n = ctypes.c_ulonglong()
         _check(lib().sem3d_launch_count(self._h, ctypes.byref(n)), "sem3d_launch_count")
         return n.value
+
+    def tuned_config(self, axis: int) -> int:
+        """FP32 kernel configuration the autotuner picked for the pass along axis."""
+        c = ctypes.c_int()
+        _check(lib().sem3d_tuned_config(self._h, axis, ctypes.byref(c)), "sem3d_tuned_config")
+        return c.value
+
+    def set_tuned_config(self, axis: int, config: int):
+        """Pin an FP32 kernel configuration for this plan's pass shape along axis."""
+        _check(lib().sem3d_set_tuned_config(self._h, axis, config), "sem3d_set_tuned_config")
 
     def nodes(self, axis: int) -> np.ndarray:
         x = np.empty(self.n[axis])

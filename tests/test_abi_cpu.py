@@ -56,6 +56,8 @@ def test_setup_argument_validation(L):
         assert L.sem3d_last_error()
     assert L.sem3d_setup(7, 7, 7, 2, 1.0, 1.0, 1.0, 0.0, None) == 1
     assert L.sem3d_set_precision(None, 0, 1) == 1
+    assert L.sem3d_tuned_config(None, 0, None) == 1
+    assert L.sem3d_set_tuned_config(None, 0, 0) == 1
     assert L.sem3d_destroy(None) == 0
 
 

@@ -39,7 +39,7 @@ def _refs(probs):
     return refs
 
 
-@pytest.mark.parametrize("mode", ["grouped_fp32", "streams_mixed"])
+@pytest.mark.parametrize("mode", ["grouped_fp32", "grouped_fp32_mixed_tiles", "streams_mixed"])
 def test_batched_matches_oracle(sem3d, mode):
     probs = _problems()
     refs = _refs(probs)
@@ -47,8 +47,12 @@ def test_batched_matches_oracle(sem3d, mode):
     try:
         for q, pr in enumerate(probs):
             p = sem3d.Plan(*pr["n3"], pr["k"], (1.0, 1.0, 1.0), pr["c"])
-            if mode == "grouped_fp32":
+            if mode.startswith("grouped_fp32"):
                 p.set_precision("fp32", 2)
+                if mode == "grouped_fp32_mixed_tiles":
+                    # one grouped launch runs problems with different tile shapes
+                    for a in range(3):
+                        p.set_tuned_config(a, (q + a) % 6)
             else:
                 p.set_precision(*[("fp32", 2), ("bf16x3", 3), ("fp64", 1)][q % 3])
             plans.append(p)

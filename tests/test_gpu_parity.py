@@ -146,6 +146,30 @@ def test_fp32_tier_matches_oracle(sem3d, i):
         assert _rel(u.cpu().numpy(), ref) < 1e-12
 
 
+@pytest.mark.parametrize("config", range(6))
+@pytest.mark.parametrize("i", [1, 3, 5])
+def test_fp32_every_kernel_configuration(sem3d, i, config):
+    # Each of the six FP32 kernel configurations (tile shape x shared-memory
+    # stages), pinned on all three passes, on grids with ragged tiles in every
+    # direction; the autotuner's pick must be one of them.
+    n3, k, L3, c, (sx, sy, sz), F = _case(i)
+    ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        p.set_precision("fp32", 0)
+        assert all(0 <= p.tuned_config(a) <= 5 for a in range(3))
+        for a in range(3):
+            p.set_tuned_config(a, config)
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.solve(f, u)
+        p.sync_check()
+        assert _rel(u.cpu().numpy(), ref) < 1e-5
+        p.set_precision("fp32", 2)
+        p.solve(f, u)
+        p.sync_check()
+        assert _rel(u.cpu().numpy(), ref) < 1e-12
+
+
 @pytest.mark.parametrize("i", [2, 4, 5])
 def test_bf16_single_product_tier(sem3d, i):
     # One bf16 product per element pair: bare ~1e-2 (measured 1.4e-2 at n = 255 and
