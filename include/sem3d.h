@@ -88,6 +88,22 @@ typedef enum {
 sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, double Lz, double c,
                          sem3d_handle* out);
 
+/* Homogeneous boundary data of a plan (Section 2.2 treats Dirichlet data by
+ * dropping the boundary nodes; the appendix assembles the Neumann problem,
+ * whose natural boundary condition keeps every node; Table 1 has both). */
+typedef enum { SEM3D_BC_DIRICHLET = 0, SEM3D_BC_NEUMANN = 1 } sem3d_bc;
+
+/* sem3d_setup with a choice of boundary condition.  SEM3D_BC_DIRICHLET is
+ * sem3d_setup.  SEM3D_BC_NEUMANN: homogeneous Neumann data du/dn = 0 on every
+ * face; the unknowns are all n = Ne*k + 1 GLL nodes of each axis, so each n
+ * must satisfy (n-1) % k == 0 and n > k, nodes run from 0 to L inclusive,
+ * and c > 0 is required (lambda = 0 belongs to the constant mode).  Neumann
+ * plans compute every refinement residual in FP64 with the per-row banded
+ * operator (SEM3D_RESIDUAL_MIXED acts as SEM3D_RESIDUAL_FP64) and do not
+ * support SEM3D_F16X3 (SEM3D_ERR_UNSUPPORTED). */
+sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly, double Lz, double c, sem3d_bc bc,
+                            sem3d_handle* out);
+
 /* Select the arithmetic of the mode products and the number of FP64
  * iterative-refinement sweeps (each sweep: FP64 residual r = f - (c + H_x (+)
  * H_y (+) H_z) u with the banded operator of Eq. 12, a solve of the correction

@@ -38,16 +38,16 @@ sem3d_status cuda_fail(cudaError_t e, const char* where) {
 // Host-side cache of 1D axis data: identical (n, k, L) axes share one eigen-
 // decomposition within a process.
 std::mutex g_axis_mu;
-std::map<std::tuple<int, int, double>, std::shared_ptr<const Axis1D>> g_axis_cache;
+std::map<std::tuple<int, int, double, int>, std::shared_ptr<const Axis1D>> g_axis_cache;
 
-std::shared_ptr<const Axis1D> get_axis(int n, int k, double L) {
-  const auto key = std::make_tuple(n, k, L);
+std::shared_ptr<const Axis1D> get_axis(int n, int k, double L, int bc) {
+  const auto key = std::make_tuple(n, k, L, bc);
   {
     std::lock_guard<std::mutex> lk(g_axis_mu);
     auto it = g_axis_cache.find(key);
     if (it != g_axis_cache.end()) return it->second;
   }
-  auto ax = std::make_shared<const Axis1D>(build_axis(n, k, L));
+  auto ax = std::make_shared<const Axis1D>(build_axis(n, k, L, bc));
   std::lock_guard<std::mutex> lk(g_axis_mu);
   g_axis_cache[key] = ax;
   return ax;
@@ -269,22 +269,32 @@ const char* sem3d_last_error(void) { return g_last_error.c_str(); }
 
 sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, double Lz, double c,
                          sem3d_handle* out) {
+  return sem3d_setup_bc(nx, ny, nz, k, Lx, Ly, Lz, c, SEM3D_BC_DIRICHLET, out);
+}
+
+sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly, double Lz, double c, sem3d_bc bc,
+                            sem3d_handle* out) {
   if (!out) return fail(SEM3D_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (k < 1 || k > 24) return fail(SEM3D_ERR_INVALID_ARG, "k must be in [1, 24]");
+  if (bc != SEM3D_BC_DIRICHLET && bc != SEM3D_BC_NEUMANN) return fail(SEM3D_ERR_INVALID_ARG, "unknown boundary condition");
   const int n3[3] = {nx, ny, nz};
   const double L3[3] = {Lx, Ly, Lz};
   for (int a = 0; a < 3; ++a) {
-    if (n3[a] < 1 || (n3[a] + 1) % k != 0)
-      return fail(SEM3D_ERR_INVALID_ARG, "each n must be >= 1 with (n+1) % k == 0");
+    if (bc == SEM3D_BC_DIRICHLET && (n3[a] < 1 || (n3[a] + 1) % k != 0))
+      return fail(SEM3D_ERR_INVALID_ARG, "Dirichlet: each n must be >= 1 with (n+1) % k == 0");
+    if (bc == SEM3D_BC_NEUMANN && (n3[a] < k + 1 || (n3[a] - 1) % k != 0))
+      return fail(SEM3D_ERR_INVALID_ARG, "Neumann: each n must be > k with (n-1) % k == 0");
     if (!(L3[a] > 0.0) || !std::isfinite(L3[a])) return fail(SEM3D_ERR_INVALID_ARG, "box lengths must be > 0");
   }
   if ((double)nx * ny * nz >= 1099511627776.0) return fail(SEM3D_ERR_INVALID_ARG, "grid too large");
   if (!std::isfinite(c)) return fail(SEM3D_ERR_INVALID_ARG, "c must be finite");
+  // With Neumann data the constant is in the kernel of -Lap (lambda = 0 on every axis).
+  if (bc == SEM3D_BC_NEUMANN && !(c > 0.0)) return fail(SEM3D_ERR_INVALID_ARG, "Neumann: c must be > 0");
   std::unique_ptr<sem3d_plan> p(new (std::nothrow) sem3d_plan());
   if (!p) return fail(SEM3D_ERR_OOM, "host allocation failed");
   try {
-    for (int a = 0; a < 3; ++a) p->ax[a] = get_axis(n3[a], k, L3[a]);
+    for (int a = 0; a < 3; ++a) p->ax[a] = get_axis(n3[a], k, L3[a], (int)bc);
   } catch (const std::exception& ex) {
     return fail(SEM3D_ERR_INVALID_ARG, std::string("axis setup failed: ") + ex.what());
   }
@@ -292,7 +302,7 @@ sem3d_status sem3d_setup(int nx, int ny, int nz, int k, double Lx, double Ly, do
   if (!(c > -lmin)) return fail(SEM3D_ERR_INVALID_ARG, "c <= -(lambda_x1 + lambda_y1 + lambda_z1): not definite");
   CUDA_TRY(cudaGetDevice(&p->device));
   CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
-  p->g.nx = nx; p->g.ny = ny; p->g.nz = nz; p->g.Px = pad16(nx); p->g.c = c;
+  p->g.nx = nx; p->g.ny = ny; p->g.nz = nz; p->g.Px = pad16(nx); p->g.c = c; p->g.bc = (int)bc;
   p->k = k;
   for (int a = 0; a < 3; ++a) p->L[a] = L3[a];
   for (int a = 0; a < 3; ++a) {
@@ -378,7 +388,8 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweep
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
   if (prec != SEM3D_FP64 && prec != SEM3D_FP32 && prec != SEM3D_BF16 && prec != SEM3D_BF16X3 && prec != SEM3D_F16X3)
     return fail(SEM3D_ERR_INVALID_ARG, "unknown precision");
-  if (prec == SEM3D_F16X3 && h->k > 8) return fail(SEM3D_ERR_UNSUPPORTED, "F16X3 needs k <= 8");
+  if (prec == SEM3D_F16X3 && (h->k > 8 || h->g.bc != 0))
+    return fail(SEM3D_ERR_UNSUPPORTED, "F16X3 needs k <= 8 and Dirichlet data");
   if (sweeps < 0 || sweeps > 16) return fail(SEM3D_ERR_INVALID_ARG, "sweeps must be in [0, 16]");
   if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16 || prec == SEM3D_F16X3) {
     int major = 0, minor = 0;
@@ -476,7 +487,7 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
     const int sw = h->sweeps;
     // Mixed residuals: sweeps 1 .. sw-1 in double-FP32 with the solution held
     // as a double-FP32 pair, the last sweep in FP64 on the FP64 solution.
-    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8 &&
+    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8 && h->g.bc == 0 &&
                        (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_F16X3);
     const bool f16 = h->prec == SEM3D_F16X3;
     // F16X3: the residual is written as FP32 into S1's storage (4 bytes per
@@ -566,7 +577,7 @@ sem3d_status sem3d_axis_info(int n, int k, double L, double* x, double* M, doubl
     return fail(SEM3D_ERR_INVALID_ARG, "need k in [1,24], n >= 1, (n+1) % k == 0, L > 0");
   std::shared_ptr<const Axis1D> ax;
   try {
-    ax = get_axis(n, k, L);
+    ax = get_axis(n, k, L, 0);
   } catch (const std::exception& ex) {
     return fail(SEM3D_ERR_INVALID_ARG, std::string("axis setup failed: ") + ex.what());
   }

@@ -568,7 +568,7 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.k = k; a.Px = g.Px; a.mode = mode; a.c = g.c;
   const long long N = (long long)g.nx * g.ny * g.nz;
   cudaError_t e;
-  switch (k) {
+  switch (g.bc == 0 ? k : 0) {  // the element-pattern kernels assume Dirichlet rows
     case 1: e = launch_elem<1>(a, ax, mode, s); break;
     case 2: e = launch_elem<2>(a, ax, mode, s); break;
     case 3: e = launch_elem<3>(a, ax, mode, s); break;
@@ -577,7 +577,7 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
     case 6: e = launch_elem<6>(a, ax, mode, s); break;
     case 7: e = launch_elem<7>(a, ax, mode, s); break;
     case 8: e = launch_elem<8>(a, ax, mode, s); break;
-    default:  // higher degrees: one thread per node, per-row band ranges
+    default:  // higher degrees and Neumann data: one thread per node, per-row band ranges
       stencil_kernel<<<(int)((N + 255) / 256 < 0x7FFFFFFF ? (N + 255) / 256 : 0x7FFFFFFF), 256, 0, s>>>(a);
       e = cudaGetLastError();
   }
@@ -590,6 +590,7 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
                               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s, float* out32,
                               F16State* st) {
+  if (g.bc != 0) return cudaErrorInvalidValue;  // element-pattern rows (Dirichlet) only
   DfArgs a{};
   a.uh = u.hi; a.ul = u.lo; a.f = f; a.hi = out_hi; a.lo = out_lo;
   a.out32 = out32; a.st = st;
@@ -618,7 +619,7 @@ cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers
 
 cudaError_t launch_stencil_f32out(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f,
                                   float* out32, F16State* st, cudaStream_t s) {
-  if (k < 1 || k > 8) return cudaErrorInvalidValue;
+  if (k < 1 || k > 8 || g.bc != 0) return cudaErrorInvalidValue;
   StencilArgs a{};
   a.u = u; a.f = f; a.out32 = out32; a.st = st;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.k = k; a.Px = g.Px; a.mode = 3; a.c = g.c;

@@ -16,9 +16,11 @@ namespace sem3d {
 
 // ---------------------------------------------------------------- host setup
 
-// 1D data of one axis: n interior nodes of degree k on [0, L], Ne = (n+1)/k.
+// 1D data of one axis of degree k on [0, L]: with homogeneous Dirichlet data
+// (bc = 0) the n = Ne*k - 1 interior nodes, with homogeneous Neumann data
+// (bc = 1) all n = Ne*k + 1 nodes (Section 2.2).
 struct Axis1D {
-  int n = 0, k = 0, Ne = 0;
+  int n = 0, k = 0, Ne = 0, bc = 0;
   double L = 0.0;
   std::vector<double> x;        // interior node coordinates
   std::vector<double> M;        // lumped mass diagonal
@@ -36,7 +38,7 @@ struct Axis1D {
 
 void gll_rule(int N, std::vector<double>& r, std::vector<double>& w);
 void gll_diff(int N, const std::vector<double>& r, std::vector<double>& D);
-Axis1D build_axis(int n, int k, double L);
+Axis1D build_axis(int n, int k, double L, int bc = 0);
 
 // ---------------------------------------------------------------- device data
 
@@ -110,6 +112,7 @@ struct Geom {
   int nx, ny, nz;
   int Px;              // pitch of x in the bf16 working arrays
   double c;
+  int bc = 0;          // 0: Dirichlet (element-pattern stencils), 1: Neumann (per-row stencil)
 };
 
 // ---- FP64 kernels (fp64_kernels.cu)

@@ -212,14 +212,20 @@ void sym_eig(int n, std::vector<double>& A, std::vector<double>& d, std::vector<
 
 }  // namespace
 
-// Build the axis data for n interior nodes of degree k on [0, L].
-Axis1D build_axis(int n, int k, double L) {
-  if (k < 1 || n < 1 || (n + 1) % k != 0) throw std::invalid_argument("need (n+1) % k == 0, n >= 1, k >= 1");
+// Build the axis data of degree k on [0, L]: n interior nodes (Dirichlet,
+// bc = 0) or all n nodes (Neumann, bc = 1).
+Axis1D build_axis(int n, int k, double L, int bc) {
+  if (k < 1 || n < 1) throw std::invalid_argument("need n >= 1, k >= 1");
+  if (bc == 0 && (n + 1) % k != 0) throw std::invalid_argument("Dirichlet: need (n+1) % k == 0");
+  if (bc == 1 && (n < k + 1 || (n - 1) % k != 0)) throw std::invalid_argument("Neumann: need (n-1) % k == 0, n > k");
+  if (bc != 0 && bc != 1) throw std::invalid_argument("unknown boundary condition");
   Axis1D ax;
   ax.n = n;
   ax.k = k;
-  ax.Ne = (n + 1) / k;
+  ax.bc = bc;
+  ax.Ne = bc == 0 ? (n + 1) / k : (n - 1) / k;
   ax.L = L;
+  const int offset = bc == 0 ? 1 : 0;  // unknown index = global node - offset
   std::vector<double> r, w, D;
   gll_rule(k, r, w);
   gll_diff(k, r, D);
@@ -233,20 +239,19 @@ Axis1D build_axis(int n, int k, double L) {
       Sloc[(size_t)p * nl + q] = s;
     }
   const double dx = L / ax.Ne, h = 0.5 * dx;
-  const int nglob = ax.Ne * k + 1;
-  // Global node g = e*k + q; unknown index = g - 1 (node 0 and node nglob-1
-  // carry the Dirichlet data and are dropped).
+  // Global node g = e*k + q; unknown index = g - offset (Dirichlet: node 0 and
+  // node Ne*k carry the boundary data and are dropped; Neumann: all kept).
   ax.x.assign(n, 0.0);
   ax.M.assign(n, 0.0);
   ax.S.assign((size_t)n * n, 0.0);
   for (int e = 0; e < ax.Ne; ++e) {
     for (int p = 0; p < nl; ++p) {
-      const int gp = e * k + p - 1;
+      const int gp = e * k + p - offset;
       if (gp < 0 || gp >= n) continue;
       ax.x[gp] = e * dx + h * (1.0 + r[p]);
       ax.M[gp] += h * w[p];
       for (int q = 0; q < nl; ++q) {
-        const int gq = e * k + q - 1;
+        const int gq = e * k + q - offset;
         if (gq < 0 || gq >= n) continue;
         ax.S[(size_t)gp * n + gq] += Sloc[(size_t)p * nl + q] / h;
       }

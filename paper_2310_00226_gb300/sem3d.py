@@ -25,6 +25,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 4, "bf16x3": 5, "f16x3": 6}
 #: Every entry point declared in include/sem3d.h.
 EXPORTS = (
     "sem3d_setup",
+    "sem3d_setup_bc",
     "sem3d_set_precision",
     "sem3d_set_residual",
     "sem3d_workspace_size",
@@ -69,6 +70,8 @@ def lib() -> ctypes.CDLL:
     c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
     L.sem3d_setup.argtypes = [c_int, c_int, c_int, c_int, c_double, c_double, c_double, c_double,
                               ctypes.POINTER(c_void_p)]
+    L.sem3d_setup_bc.argtypes = [c_int, c_int, c_int, c_int, c_double, c_double, c_double, c_double, c_int,
+                                 ctypes.POINTER(c_void_p)]
     L.sem3d_set_precision.argtypes = [c_void_p, c_int, c_int]
     L.sem3d_set_residual.argtypes = [c_void_p, c_int]
     L.sem3d_workspace_size.argtypes = [c_void_p, ctypes.POINTER(c_size_t)]
@@ -146,11 +149,14 @@ def solve_batched(plans, fs, us, stream=None):
 class Plan:
     """A libsem3d plan (sem3d_setup ... sem3d_destroy)."""
 
-    def __init__(self, nx: int, ny: int, nz: int, k: int, L=(1.0, 1.0, 1.0), c: float = 0.0):
+    BCS = {"dirichlet": 0, "neumann": 1}
+
+    def __init__(self, nx: int, ny: int, nz: int, k: int, L=(1.0, 1.0, 1.0), c: float = 0.0, bc: str = "dirichlet"):
         h = ctypes.c_void_p()
-        _check(lib().sem3d_setup(nx, ny, nz, k, float(L[0]), float(L[1]), float(L[2]), float(c), ctypes.byref(h)),
-               "sem3d_setup")
+        _check(lib().sem3d_setup_bc(nx, ny, nz, k, float(L[0]), float(L[1]), float(L[2]), float(c), self.BCS[bc],
+                                    ctypes.byref(h)), "sem3d_setup_bc")
         self._h = h
+        self.bc = bc
         self.shape = (nz, ny, nx)
         self.n = (nx, ny, nz)
         self.k = k

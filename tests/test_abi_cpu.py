@@ -56,6 +56,13 @@ def test_setup_argument_validation(L):
         assert L.sem3d_last_error()
     assert L.sem3d_setup(7, 7, 7, 2, 1.0, 1.0, 1.0, 0.0, None) == 1
     assert L.sem3d_set_precision(None, 0, 1) == 1
+    h = ctypes.c_void_p()
+    # Neumann: (n-1) % k == 0, n > k and c > 0; an unknown boundary condition is rejected
+    assert L.sem3d_setup_bc(8, 9, 9, 2, 1.0, 1.0, 1.0, 1.0, 1, ctypes.byref(h)) == 1
+    assert L.sem3d_setup_bc(1, 9, 9, 2, 1.0, 1.0, 1.0, 1.0, 1, ctypes.byref(h)) == 1
+    assert L.sem3d_setup_bc(9, 9, 9, 2, 1.0, 1.0, 1.0, 0.0, 1, ctypes.byref(h)) == 1
+    assert b"c must be > 0" in L.sem3d_last_error()
+    assert L.sem3d_setup_bc(7, 7, 7, 2, 1.0, 1.0, 1.0, 1.0, 2, ctypes.byref(h)) == 1
     assert L.sem3d_tuned_config(None, 0, None) == 1
     assert L.sem3d_set_tuned_config(None, 0, 0) == 1
     assert L.sem3d_destroy(None) == 0
