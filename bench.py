@@ -368,7 +368,7 @@ def run_workload(args, rank: int):
     stream = torch.cuda.current_stream()
     line = {"workload": args.workload, "n_gpus": 1, "data": "synthetic", "higher_is_better": True}
     if args.workload == "batched":
-        probs = batched_helmholtz(64)
+        probs = batched_helmholtz(args.batch_count)
         plans, fs, us = [], [], []
         for pr in probs:
             p = sem3d.Plan(*pr["n3"], pr["k"], (1.0, 1.0, 1.0), pr["c"])
@@ -385,11 +385,11 @@ def run_workload(args, rank: int):
             plans[0].sync_check(stream)
             res[prec] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": sweeps,
                          "path": "grouped launches" if prec == "fp32" else "stream pool"}
-        line.update({"metric": "64 batched Helmholtz solves (uneven n in {63..511}, k in {2,3,4,6}): GDoF/s",
+        line.update({"metric": f"{args.batch_count} batched Helmholtz solves (uneven n in {{63..511}}, k in {{2,3,4,6}}): GDoF/s",
                      "value": res["fp32"]["GDoF_per_s"], "unit": "GDoF/s", "total_dofs": dofs, "tiers": res,
                      "steps": args.steps, "warmup": args.warmup})
     elif args.workload == "ch":
-        n, k = 511, 2
+        n, k = args.workload_n or 511, 2
         p = sem3d.Plan(n, n, n, k, (2 * np.pi,) * 3, 0.0)
         rng = np.random.Generator(np.random.PCG64(20231001))
         phi0 = torch.from_numpy(rng.uniform(-0.05, 0.05, (n, n, n))).cuda()
@@ -406,11 +406,11 @@ def run_workload(args, rank: int):
             ms = (time.perf_counter() - t0) * 1e3 / steps
             p.sync_check(stream)
             res[prec] = {"ms_per_step": ms, "steps": steps, "max_abs_phi": float(pn.abs().max())}
-        line.update({"metric": "Cahn-Hilliard BDF2 step, Q^2 n=511 on [0,2pi]^3 (1.33e8 DoF): ms/step",
+        line.update({"metric": f"Cahn-Hilliard BDF2 step, Q^2 n={n} on [0,2pi]^3 ({n**3:.3g} DoF): ms/step",
                      "value": res["bf16x3"]["ms_per_step"], "unit": "ms/step", "higher_is_better": False,
                      "tiers": res, "params": {"eps": 0.05, "m": 1.0, "dt": 1e-4, "S": 2.0}})
     elif args.workload == "pcg":
-        n, k = 1023, 4
+        n, k = args.workload_n or 1023, 4
         p = sem3d.Plan(n, n, n, k, (1.0, 1.0, 1.0), 25.0)
         x = p.nodes(0)
         V = torch.from_numpy(harmonic_potential(x, x, x, 100.0)).cuda()
@@ -425,7 +425,7 @@ def run_workload(args, rank: int):
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3
             res[f"{prec}_sweeps{sweeps}"] = {"ms": ms, "iterations": it, "relres": rr, "ms_per_iteration": ms / it}
-        line.update({"metric": "Schroedinger -Lap u + 100|x-1/2|^2 u = 1, Q^4 n=1023 (1.07e9 DoF), PCG to 1e-10: s",
+        line.update({"metric": f"Schroedinger -Lap u + 100|x-1/2|^2 u = 1, Q^4 n={n} ({n**3:.3g} DoF), PCG to 1e-10: s",
                      "value": min(r["ms"] for r in res.values()) / 1e3, "unit": "s", "higher_is_better": False,
                      "preconditioner": res})
     if rank == 0:
@@ -452,6 +452,9 @@ def main():
     ap.add_argument("--workload", choices=["solve", "batched", "ch", "pcg"], default="solve",
                     help="solve = the headline n=999 solve; the others time the batched, Cahn-Hilliard and PCG workloads")
     ap.add_argument("--ch-steps", type=int, default=1000)
+    ap.add_argument("--workload-n", type=int, default=None,
+                    help="grid size of the ch (default 511) or pcg (default 1023) workload, for small profiling runs")
+    ap.add_argument("--batch-count", type=int, default=64, help="problems in the batched workload")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
