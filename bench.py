@@ -173,6 +173,20 @@ def run_reference(args, rank: int, world: int):
 
 # --------------------------------------------------------------------- our path
 
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The slowest rank's time (all ranks get it): the job's time for a weak-scaled
+    replicated step.  device: "cuda" with NCCL, "cpu" with gloo."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the job's time (per second)."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def timed(fn, steps, warmup, stream, torch, dist=None):
     for _ in range(warmup):
         fn()
@@ -188,9 +202,7 @@ def timed(fn, steps, warmup, stream, torch, dist=None):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
     return ms
 
@@ -258,7 +270,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         plan.set_residual("fp64")
         ms_r = timed(step, args.fp64_residual_steps, 1, stream, torch, dist)
         plan.sync_check(stream)
-        f64res = {"ms_per_step": ms_r, "value": dofs * world / (ms_r / 1e3) / 1e9, "unit": "GDoF/s",
+        f64res = {"ms_per_step": ms_r, "value": job_throughput(dofs, world, ms_r) / 1e9, "unit": "GDoF/s",
                   "steps": args.fp64_residual_steps, "warmup": 1,
                   "rel_linf_vs_mixed": float((u - u_bf).abs().max() / u_bf.abs().max())}
         plan.set_residual(args.residual)
@@ -273,7 +285,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         plan.profile(False)
         plan.sync_check(stream)
         diff = float((u - u_bf).abs().max() / u.abs().max())
-        fp64 = {"ms_per_step": ms64, "value": dofs * world / (ms64 / 1e3) / 1e9, "unit": "GDoF/s",
+        fp64 = {"ms_per_step": ms64, "value": job_throughput(dofs, world, ms64) / 1e9, "unit": "GDoF/s",
                 "steps": args.fp64_steps, "warmup": args.fp64_warmup, "path": "FP64 DMMA mode products + 1 FP64 sweep",
                 "rel_linf_bf16x3_vs_fp64": diff, "speedup_bf16x3_over_fp64": ms64 / ms,
                 "dmma_kernel_avg_ms": f64_ms / max(1, f64_n),
@@ -292,7 +304,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             u_pin.copy_(u, non_blocking=True)
 
         ms_e2e = timed(e2e_step, args.steps, args.warmup, stream, torch, dist)
-        e2e = {"value": dofs * world / (ms_e2e / 1e3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms_e2e,
+        e2e = {"value": job_throughput(dofs, world, ms_e2e) / 1e9, "unit": "GDoF/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)}
         del f_pin, u_pin
 
@@ -324,7 +336,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                           f"{n}/{args.oracle_lines}); {spent:.1f} s of CPU work")}
 
     line = {
-        "metric": METRIC, "value": dofs * world / (ms / 1e3) / 1e9, "unit": "GDoF/s", "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(dofs, world, ms) / 1e9, "unit": "GDoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate) + f64 refinement", "data": "synthetic",
         "config": {"workload": f"q4_n{n}_expsine: Q^4, Ne={(n + 1) // k}/axis on [0,1]^3, n={n}, {dofs} DoF, "
