@@ -22,6 +22,11 @@ int ch_grid(long long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// Grid of the line kernels: a block walks lines blockIdx.x, + gridDim.x, ...;
+// 16 blocks per SM (two waves of 8 resident), so that block launches are few
+// against the work (a line of Px elements is only 2-4 elements per thread).
+int line_grid(long long lines) { return (int)(lines < 152LL * 16 ? (lines < 1 ? 1 : lines) : 152LL * 16); }
+
 __device__ __forceinline__ void split2f(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
   h = __float2bfloat16_rn(v);
   l = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -39,26 +44,46 @@ __global__ void __launch_bounds__(CH_THREADS) ch_prep_kernel(const double* phi_n
   }
 }
 
-// Split-bf16 inputs (pitch Px, zero pads), FP32 arithmetic.
+// FP64 -> FP32 with round-to-nearest-even, in integer arithmetic from the
+// IEEE 754 binary64/binary32 formats (the hardware conversion runs on the FP64
+// pipe, 1/64 of the FP32 rate on this GPU).  Results in the FP32 normal range
+// (and overflow to infinity) are formed here; the rare subnormal results and
+// NaN inputs take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;  // biased FP32 exponent
+  if (e <= 0 || ((b >> 52) & 0x7FF) == 0x7FF) return __double2float_rn(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned int r = ((unsigned int)e << 23) | (unsigned int)(m >> 29);  // truncated
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull), half = 0x10000000u;
+  r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;  // a carry rounds into the exponent
+  return __uint_as_float(sign | r);
+}
+
+// Split-bf16 inputs (pitch Px, zero pads), FP32 arithmetic.  Blocks walk the
+// (j, l) lines, their threads along i.
 __global__ void __launch_bounds__(CH_THREADS) ch_prep_split_kernel(const double* phi_n, const double* phi_nm1,
                                                                    __nv_bfloat16* gh_hi, __nv_bfloat16* gh_lo,
                                                                    __nv_bfloat16* g_hi, __nv_bfloat16* g_lo, int nx,
                                                                    int Px, long long lines, ChParams c) {
-  const long long total = lines * Px;
   const float S = (float)c.S, inv_eps = (float)(1.0 / c.eps);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long line = e / Px;
-    const int i = (int)(e - line * Px);
-    float gh = 0.f, gg = 0.f;
-    if (i < nx) {
-      const float pn = (float)phi_n[line * nx + i], pm = (float)phi_nm1[line * nx + i];
-      const float bar = 2.f * pn - pm;
-      gh = 2.f * pn - 0.5f * pm;
-      gg = (bar * bar * bar - bar - S * bar) * inv_eps;
+  for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
+    const double* pn_row = phi_n + line * nx;
+    const double* pm_row = phi_nm1 + line * nx;
+    const long long o = line * Px;
+    for (int i = threadIdx.x; i < Px; i += blockDim.x) {
+      float gh = 0.f, gg = 0.f;
+      if (i < nx) {
+        const float pn = f64_to_f32_rn(pn_row[i]), pm = f64_to_f32_rn(pm_row[i]);
+        const float bar = 2.f * pn - pm;
+        gh = 2.f * pn - 0.5f * pm;
+        gg = (bar * bar * bar - bar - S * bar) * inv_eps;
+      }
+      split2f(gh, gh_hi[o + i], gh_lo[o + i]);
+      split2f(gg, g_hi[o + i], g_lo[o + i]);
     }
-    split2f(gh, gh_hi[e], gh_lo[e]);
-    split2f(gg, g_hi[e], g_lo[e]);
   }
 }
 
@@ -80,20 +105,20 @@ __global__ void __launch_bounds__(CH_THREADS) ch_combine_split_kernel(
     const __nv_bfloat16* a1h, const __nv_bfloat16* a1l, const __nv_bfloat16* a2h, const __nv_bfloat16* a2l,
     __nv_bfloat16* oh, __nv_bfloat16* ol, const float* lx, const float* ly, const float* lz, int nx, int ny, int Px,
     long long lines, ChParams c) {
-  const long long total = lines * Px;
   const float dtm = (float)(c.dt * c.m), eps = (float)c.eps, s_eps = (float)(c.S / c.eps);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long line = e / Px;
-    const int i = (int)(e - line * Px);
-    float v = 0.f;
-    if (i < nx) {
-      const float L = lx[i] + ly[line % ny] + lz[line / ny];
-      const float x1 = __bfloat162float(a1h[e]) + __bfloat162float(a1l[e]);
-      const float x2 = __bfloat162float(a2h[e]) + __bfloat162float(a2l[e]);
-      v = (x1 - dtm * L * x2) / (1.5f + dtm * (eps * L * L + s_eps * L));
+  for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
+    const float lyz = ly[line % ny] + lz[line / ny];  // block-uniform
+    const long long o = line * Px;
+    for (int i = threadIdx.x; i < Px; i += blockDim.x) {
+      float v = 0.f;
+      if (i < nx) {
+        const float L = lx[i] + lyz;
+        const float x1 = __bfloat162float(a1h[o + i]) + __bfloat162float(a1l[o + i]);
+        const float x2 = __bfloat162float(a2h[o + i]) + __bfloat162float(a2l[o + i]);
+        v = (x1 - dtm * L * x2) / (1.5f + dtm * (eps * L * L + s_eps * L));
+      }
+      split2f(v, oh[o + i], ol[o + i]);
     }
-    split2f(v, oh[e], ol[e]);
   }
 }
 
@@ -110,8 +135,8 @@ cudaError_t launch_ch_prep(int tier, const Geom& g, const double* phi_n, const d
                                                               static_cast<float*>(gg), N, c);
   } else {
     const long long lines = (long long)g.ny * g.nz;
-    ch_prep_split_kernel<<<ch_grid(lines * g.Px), CH_THREADS, 0, s>>>(phi_n, phi_nm1, sh.hi, sh.lo, sg.hi, sg.lo,
-                                                                       g.nx, g.Px, lines, c);
+    ch_prep_split_kernel<<<line_grid(lines), CH_THREADS, 0, s>>>(phi_n, phi_nm1, sh.hi, sh.lo, sg.hi, sg.lo, g.nx,
+                                                                  g.Px, lines, c);
   }
   return cudaGetLastError();
 }
@@ -129,7 +154,7 @@ cudaError_t launch_ch_combine(int tier, const Geom& g, const DevAxis* ax, const 
         ax[1].lam, ax[2].lam, g.nx, g.ny, N, c);
   } else {
     const long long lines = (long long)g.ny * g.nz;
-    ch_combine_split_kernel<<<ch_grid(lines * g.Px), CH_THREADS, 0, s>>>(
+    ch_combine_split_kernel<<<line_grid(lines), CH_THREADS, 0, s>>>(
         s1.hi, s1.lo, s2.hi, s2.lo, so.hi, so.lo, ax[0].lamf, ax[1].lamf, ax[2].lamf, g.nx, g.ny, g.Px, lines, c);
   }
   return cudaGetLastError();
