@@ -174,7 +174,7 @@ size_t workspace_bytes(const sem3d_plan* p) {
   if (p->prec == SEM3D_FP64) return 3 * align256(N * sizeof(double));
   if (p->prec == SEM3D_FP32) return 2 * align256(N * sizeof(float)) + align256(N * sizeof(double));
   const size_t Ns = (size_t)p->g.Px * p->g.ny * p->g.nz;
-  return 6 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(N * sizeof(float));
+  return 6 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(Ns * sizeof(float));
 }
 
 sem3d_status ensure_workspace(sem3d_plan* p) {
@@ -327,6 +327,8 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
         hh[q] = (float)hq[q];
         hl[q] = (float)(hq[q] - (double)hh[q]);
       }
+      if (k <= 4)
+        for (size_t q = 0; q < hq.size(); ++q) { D.Hq_hi_host[q] = hh[q]; D.Hq_lo_host[q] = hl[q]; }
       if ((st = dev_upload(p.get(), &D.Hq_hi, hh.data(), hh.size())) != SEM3D_OK) return st;
       if ((st = dev_upload(p.get(), &D.Hq_lo, hl.data(), hl.size())) != SEM3D_OK) return st;
     }
@@ -478,7 +480,7 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
     }
   } else {
     const size_t Ns = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(__nv_bfloat16));
-    const size_t Nf = align256(N * sizeof(float));
+    const size_t Nf = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(float));  // double-FP32 u, pitch Px
     char* w = static_cast<char*>(h->ws);
     TcBuffers S0{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
     TcBuffers S1{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
@@ -517,8 +519,10 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
           LAUNCH(h, K_STENCIL, 1, s, launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16));
           LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
         } else {
-          LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
-                 launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
+          // k in {1, 2, 4}: one vector kernel that also writes the pads; otherwise
+          // the element kernel plus a pad-zeroing kernel when Px > nx
+          const int df_launches = (h->k == 1 || h->k == 2 || h->k == 4 || h->g.Px == h->g.nx) ? 1 : 2;
+          LAUNCH(h, K_STENCIL, df_launches, s, launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
         }
         const bool last_df = (q == sw - 1);
         if ((st = solve_once_bf16x3(h, S0, S1, last_df ? u : nullptr, last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, D,

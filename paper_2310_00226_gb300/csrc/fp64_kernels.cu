@@ -384,22 +384,22 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
   constexpr int BW = 2 * K + 1;
   const long long lines = (long long)a.ny * a.nz;
   const long long total = (long long)a.nex * lines;
-  const long long plane = (long long)a.nx * a.ny;
   float rmax = 0.f;  // FP32 output: max |r| of this thread's nodes
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int ex = (int)(t % a.nex);
     const long long jl = t / a.nex;
     const int j = (int)(jl % a.ny), l = (int)(jl / a.ny);
-    const long long line = jl * a.nx;
+    const long long line = jl * a.nx;    // f (pitch nx)
+    const long long uline = jl * a.Px;   // u (pitch Px)
     const int i0 = ex * K - 1;
     float wh[BW], wl[BW];
 #pragma unroll
     for (int d = 0; d < BW; ++d) {
       const int i = i0 - K + d;
       const bool ok = i >= 0 && i < a.nx;
-      wh[d] = ok ? __ldg(a.uh + line + i) : 0.f;
-      wl[d] = ok ? __ldg(a.ul + line + i) : 0.f;
+      wh[d] = ok ? __ldg(a.uh + uline + i) : 0.f;
+      wl[d] = ok ? __ldg(a.ul + uline + i) : 0.f;
     }
     float ah[K], al[K];
 #pragma unroll
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
         const int jj = j + d;
         if (jj < 0 || jj >= a.ny) continue;
         const float ch = __ldg(a.Hyh + qy * BW + d + K), cl = __ldg(a.Hyl + qy * BW + d + K);
-        const long long off = ((long long)l * a.ny + jj) * a.nx;
+        const long long off = ((long long)l * a.ny + jj) * a.Px;
 #pragma unroll
         for (int q = 0; q < K; ++q) {
           const int i = i0 + q;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
         const int ll = l + d;
         if (ll < 0 || ll >= a.nz) continue;
         const float ch = __ldg(a.Hzh + qz * BW + d + K), cl = __ldg(a.Hzl + qz * BW + d + K);
-        const long long off = (long long)ll * plane + (long long)j * a.nx;
+        const long long off = ((long long)ll * a.ny + j) * a.Px;
 #pragma unroll
         for (int q = 0; q < K; ++q) {
           const int i = i0 + q;
@@ -475,6 +475,135 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
     rmax = warp_max(rmax);
     if ((threadIdx.x & 31) == 0 && rmax > 0.f) atomicMax(&a.st->maxbits[0], __float_as_uint(rmax));
   }
+}
+
+// Rows of H per local index for the vector residual (k <= 4), as kernel
+// parameters: the x rows are read at compile-time offsets (no load
+// instructions), the y and z rows at warp-uniform offsets.
+struct DfCoef {
+  float h[3][4 * 9];
+  float l[3][4 * 9];
+};
+
+// Double-FP32 residual for k in {1, 2, 4}.  A lane handles the 4 consecutive
+// nodes i = 4c .. 4c+3 of one (j, l) line -- one float4 of each of u_hi and
+// u_lo, whose rows (pitch Px, a multiple of 16) are 16-byte aligned and whose
+// pad columns are zero -- and a warp handles one line, its lanes striding over
+// the line's Px/4 chunks.  Since 4 % k == 0, node 4c+p has the local index
+// (p+1) % k for every c: each position's x row of H is known at compile time
+// and only its band is summed.  The y and z rows depend on the warp's (j, l).
+template <int K>
+__global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __grid_constant__ DfCoef cf) {
+  constexpr int BW = 2 * K + 1;
+  const int lane = threadIdx.x & 31;
+  const long long lines = (long long)a.ny * a.nz;
+  const int chunks = a.Px >> 2;
+  const long long splane = (long long)a.ny * chunks;  // float4 per z-plane
+  const float4* UH = reinterpret_cast<const float4*>(a.uh);
+  const float4* UL = reinterpret_cast<const float4*>(a.ul);
+  float rmax = 0.f;
+  for (long long line = (long long)blockIdx.x * 8 + (threadIdx.x >> 5); line < lines;
+       line += (long long)gridDim.x * 8) {  // warp-uniform
+    const int j = (int)(line % a.ny), l = (int)(line / a.ny);
+    const int qy = (j + 1) % K, qz = (l + 1) % K;
+    const int ylo = (qy == 0) ? -K : -qy, yhi = (qy == 0) ? K : K - qy;
+    const int zlo = (qz == 0) ? -K : -qz, zhi = (qz == 0) ? K : K - qz;
+    const long long row4 = line * chunks;
+    const double* frow = a.f + line * a.nx;
+    for (int c = lane; c < chunks; c += 32) {
+      const int i0 = 4 * c;
+      float ah[4], al[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (i0 + p < a.nx) f64_to_df(__ldg(frow + i0 + p), ah[p], al[p]);
+        else { ah[p] = 0.f; al[p] = 0.f; }
+      }
+      // x: nodes i0-4 .. i0+7 (the neighbouring chunks; zero outside the line)
+      float wh[12], wl[12];
+      {
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ph = c > 0 ? __ldg(UH + row4 + c - 1) : z4, pl = c > 0 ? __ldg(UL + row4 + c - 1) : z4;
+        const float4 ch = __ldg(UH + row4 + c), cl = __ldg(UL + row4 + c);
+        const float4 nh = c + 1 < chunks ? __ldg(UH + row4 + c + 1) : z4;
+        const float4 nl = c + 1 < chunks ? __ldg(UL + row4 + c + 1) : z4;
+        wh[0] = ph.x; wh[1] = ph.y; wh[2] = ph.z; wh[3] = ph.w; wh[4] = ch.x; wh[5] = ch.y;
+        wh[6] = ch.z; wh[7] = ch.w; wh[8] = nh.x; wh[9] = nh.y; wh[10] = nh.z; wh[11] = nh.w;
+        wl[0] = pl.x; wl[1] = pl.y; wl[2] = pl.z; wl[3] = pl.w; wl[4] = cl.x; wl[5] = cl.y;
+        wl[6] = cl.z; wl[7] = cl.w; wl[8] = nl.x; wl[9] = nl.y; wl[10] = nl.z; wl[11] = nl.w;
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int q = (p + 1) % K;
+        const int dlo = (q == 0) ? -K : -q, dhi = (q == 0) ? K : K - q;
+#pragma unroll
+        for (int d = -K; d <= K; ++d)
+          if (d >= dlo && d <= dhi)  // compile-time after unrolling
+            df_sub_prod(ah[p], al[p], cf.h[0][q * BW + d + K], cf.l[0][q * BW + d + K], wh[4 + p + d], wl[4 + p + d]);
+      }
+      // y and z: the rows of the neighbouring lines, one float4 pair per row
+#pragma unroll
+      for (int d = -K; d <= K; ++d) {
+        if (d < ylo || d > yhi || j + d < 0 || j + d >= a.ny) continue;  // warp-uniform
+        const float chh = cf.h[1][qy * BW + d + K], cll = cf.l[1][qy * BW + d + K];
+        const float4 vh = __ldg(UH + row4 + (long long)d * chunks + c), vl = __ldg(UL + row4 + (long long)d * chunks + c);
+        df_sub_prod(ah[0], al[0], chh, cll, vh.x, vl.x);
+        df_sub_prod(ah[1], al[1], chh, cll, vh.y, vl.y);
+        df_sub_prod(ah[2], al[2], chh, cll, vh.z, vl.z);
+        df_sub_prod(ah[3], al[3], chh, cll, vh.w, vl.w);
+      }
+#pragma unroll
+      for (int d = -K; d <= K; ++d) {
+        if (d < zlo || d > zhi || l + d < 0 || l + d >= a.nz) continue;  // warp-uniform
+        const float chh = cf.h[2][qz * BW + d + K], cll = cf.l[2][qz * BW + d + K];
+        const float4 vh = __ldg(UH + row4 + (long long)d * splane + c);
+        const float4 vl = __ldg(UL + row4 + (long long)d * splane + c);
+        df_sub_prod(ah[0], al[0], chh, cll, vh.x, vl.x);
+        df_sub_prod(ah[1], al[1], chh, cll, vh.y, vl.y);
+        df_sub_prod(ah[2], al[2], chh, cll, vh.z, vl.z);
+        df_sub_prod(ah[3], al[3], chh, cll, vh.w, vl.w);
+      }
+      float r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) r[p] = (i0 + p < a.nx) ? ah[p] + al[p] : 0.f;  // pads stay zero
+      const long long o = line * a.Px + i0;
+      if (a.out32) {
+        *reinterpret_cast<float4*>(a.out32 + o) = make_float4(r[0], r[1], r[2], r[3]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) rmax = fmaxf(rmax, fabsf(r[p]));
+      } else {
+        uint32_t hw[2], lw[2];
+#pragma unroll
+        for (int p = 0; p < 4; p += 2) {
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(r[p]), h1 = __float2bfloat16_rn(r[p + 1]);
+          const __nv_bfloat16 l0 = __float2bfloat16_rn(r[p] - __bfloat162float(h0));
+          const __nv_bfloat16 l1 = __float2bfloat16_rn(r[p + 1] - __bfloat162float(h1));
+          hw[p / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          lw[p / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        *reinterpret_cast<uint2*>(a.hi + o) = make_uint2(hw[0], hw[1]);
+        *reinterpret_cast<uint2*>(a.lo + o) = make_uint2(lw[0], lw[1]);
+      }
+    }
+  }
+  if (a.out32) {  // every lane of the warp gets here
+    rmax = warp_max(rmax);
+    if ((threadIdx.x & 31) == 0 && rmax > 0.f) atomicMax(&a.st->maxbits[0], __float_as_uint(rmax));
+  }
+}
+
+template <int K>
+cudaError_t launch_df4(const DfArgs& a, const DevAxis* ax, cudaStream_t s) {
+  DfCoef cf{};
+  for (int w = 0; w < 3; ++w)
+    for (int e = 0; e < K * (2 * K + 1); ++e) { cf.h[w][e] = ax[w].Hq_hi_host[e]; cf.l[w][e] = ax[w].Hq_lo_host[e]; }
+  // One block per 8 consecutive lines and no grid stride: the resident blocks
+  // then sweep the grid plane by plane, so the rows 1..K planes away that a
+  // warp reads were read moments earlier by other warps and are still in L2.
+  const long long lines = (long long)a.ny * a.nz;
+  long long blocks = (lines + 7) / 8;
+  if (blocks > 0x7FFFFFFFLL) blocks = 0x7FFFFFFFLL;
+  stencil_df4_kernel<K><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a, cf);
+  return cudaGetLastError();
 }
 
 template <int K>
@@ -601,10 +730,10 @@ cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers
   a.nex = (g.nx + 1) / k;
   cudaError_t e;
   switch (k) {
-    case 1: e = launch_df<1>(a, s); break;
-    case 2: e = launch_df<2>(a, s); break;
+    case 1: return launch_df4<1>(a, ax, s);  // pads written as zeros
+    case 2: return launch_df4<2>(a, ax, s);
+    case 4: return launch_df4<4>(a, ax, s);
     case 3: e = launch_df<3>(a, s); break;
-    case 4: e = launch_df<4>(a, s); break;
     case 5: e = launch_df<5>(a, s); break;
     case 6: e = launch_df<6>(a, s); break;
     case 7: e = launch_df<7>(a, s); break;

@@ -58,6 +58,8 @@ struct DevAxis {
   double* Hq = nullptr;         // FP64 k x (2k+1) per-local-index rows of H (x axis: + c on the diagonal)
   float* Hq_hi = nullptr;       // the same table as a double-FP32 pair: Hq = Hq_hi + Hq_lo
   float* Hq_lo = nullptr;
+  float Hq_hi_host[4 * 9] = {}; // host copies for k <= 4 (kernel parameters of the vector residual)
+  float Hq_lo_host[4 * 9] = {};
   int* band_lo = nullptr;
   int* band_hi = nullptr;
   float* Wf[2] = {nullptr, nullptr};            // FP32 copies: [0] = T^{-1}, [1] = T; n x n row-major
@@ -101,7 +103,8 @@ struct F16Pass {
   float div_bound;
 };
 
-// Solution in double-FP32 form between refinement sweeps: u = hi + lo.
+// Solution in double-FP32 form between refinement sweeps: u = hi + lo, both
+// at pitch Px (x fastest) with zero pad columns i >= nx.
 struct DfBuffers {
   float* hi;
   float* lo;
@@ -147,9 +150,10 @@ cudaError_t launch_mode_product_f32_grouped(int count, const Geom* geoms, int ax
 cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f, double* out64,
                            __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, int mode, cudaStream_t s);
 // r = f - (c + H_x (+) H_y (+) H_z) u in double-FP32 arithmetic (about 48
-// significant bits), u given as a double-FP32 pair, f as FP64; r written as
-// bf16 hi/lo at pitch Px.  Needs 1 <= k <= 8 (returns cudaErrorInvalidValue
-// otherwise).
+// significant bits), u given as a double-FP32 pair (pitch Px, zero pads), f as
+// FP64 (pitch nx); r written as bf16 hi/lo at pitch Px with zero pads, or as
+// FP32 (out32).  Needs 1 <= k <= 8 and Dirichlet rows (returns
+// cudaErrorInvalidValue otherwise).
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
                               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s,
                               float* out32 = nullptr, F16State* st = nullptr);

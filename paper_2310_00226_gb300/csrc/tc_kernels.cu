@@ -400,27 +400,31 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     }
   }
   if (MODE == OUT_DF_STORE || MODE == OUT_DF_ACCUM || MODE == OUT_DF_ACCUM_F64) {
-    if (i >= a.nx) return;
-    size_t base, cs64;
-    if (PASS == 1) { base = (size_t)i + (size_t)a.nx * a.ny * batch; cs64 = (size_t)a.nx; }
-    else { base = (size_t)i + (size_t)a.nx * j; cs64 = (size_t)a.nx * a.ny; }
-    const size_t o0 = base + (size_t)col0 * cs64;
+    // z pass only: row = i + Px*j is also the index of (i, j, 0) in the
+    // double-FP32 arrays (pitch Px); the FP64 solution has pitch nx.  The
+    // store writes zeros into the pad columns i >= nx (the residual stencil
+    // reads them as the zero boundary values); the updates leave them alone.
+    if (MODE != OUT_DF_STORE && i >= a.nx) return;
+    const size_t dcs = (size_t)a.Px * a.ny;
+    const size_t d0 = (size_t)row + (size_t)col0 * dcs;
+    const size_t cs64 = (size_t)a.nx * a.ny;
+    const size_t o0 = (size_t)i + (size_t)a.nx * j + (size_t)col0 * cs64;
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
       float oh[16], ol[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const bool ok = full || col0 + h + q < a.nout;
-        oh[q] = (MODE != OUT_DF_STORE && ok) ? a.df_hi[o0 + (size_t)(h + q) * cs64] : 0.f;
-        ol[q] = (MODE != OUT_DF_STORE && ok) ? a.df_lo[o0 + (size_t)(h + q) * cs64] : 0.f;
+        oh[q] = (MODE != OUT_DF_STORE && ok) ? a.df_hi[d0 + (size_t)(h + q) * dcs] : 0.f;
+        ol[q] = (MODE != OUT_DF_STORE && ok) ? a.df_lo[d0 + (size_t)(h + q) * dcs] : 0.f;
       }
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         if (!(full || col0 + h + q < a.nout)) continue;
-        const size_t o = o0 + (size_t)(h + q) * cs64;
+        const size_t d = d0 + (size_t)(h + q) * dcs;
         if (MODE == OUT_DF_STORE) {
-          a.df_hi[o] = v[h + q];
-          a.df_lo[o] = 0.f;
+          a.df_hi[d] = i < a.nx ? v[h + q] : 0.f;
+          a.df_lo[d] = 0.f;
         } else {
           // (oh + ol) + v: two-sum of the leading parts, then renormalise.
           const float sum = oh[q] + v[h + q];
@@ -430,10 +434,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
           const float nh = sum + t;
           const float nl = t - (nh - sum);
           if (MODE == OUT_DF_ACCUM) {
-            a.df_hi[o] = nh;
-            a.df_lo[o] = nl;
+            a.df_hi[d] = nh;
+            a.df_lo[d] = nl;
           } else {
-            a.out64[o] = f32_to_f64(nh) + f32_to_f64(nl);
+            a.out64[o0 + (size_t)(h + q) * cs64] = f32_to_f64(nh) + f32_to_f64(nl);
           }
         }
       }
