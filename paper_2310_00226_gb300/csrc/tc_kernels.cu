@@ -47,8 +47,12 @@ constexpr int B_TILE_BYTES = BN * BK * 2;  // 16 KB
 constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 2 * BN;  // 512
-constexpr int EPI_WARPS = 8;                       // two per TMEM lane quadrant
-constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA, epilogue
+// Epilogue warps: two per TMEM lane quadrant for the split-bf16 outputs; four
+// for the outputs that read and write FP64 / double-FP32 solution arrays
+// (12-16 more bytes per element), which need more loads in flight to keep up
+// with the MMAs.  Threads: producer warp, MMA warp, epilogue warps.
+__host__ __device__ constexpr int epi_warps(int mode) { return mode >= 2 ? 16 : 8; }
+__host__ __device__ constexpr int num_threads(int mode) { return 64 + 32 * epi_warps(mode); }
 constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s per wait
 
 // ---------------------------------------------------------------- PTX helpers
@@ -313,6 +317,10 @@ template <int PASS, int MODE, int NP, int FMT>
 __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32],
                                                float sc_in, float sc_out, float& vmax) {
   const bool full = col0 + 32 <= a.nout;
+  // Read-modify-write batches: loads of HB elements are issued before their
+  // stores (independent, but the compiler cannot prove it through one
+  // pointer); 16 with 8 epilogue warps, 8 with 16 (the register budget halves).
+  constexpr int HB = epi_warps(MODE) > 8 ? (MODE == OUT_DF_ACCUM ? 4 : 8) : 16;
   if (FMT == 1) {
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] *= sc_in;
@@ -342,13 +350,13 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
       // the compiler cannot prove it through one pointer and would otherwise
       // serialise one memory round trip per element.
 #pragma unroll
-      for (int h = 0; h < 32; h += 16) {
-        double old[16];
+      for (int h = 0; h < 32; h += HB) {
+        double old[HB];
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
+        for (int q = 0; q < HB; ++q)
           old[q] = (MODE == OUT_F64_ACCUM && (full || col0 + h + q < a.nout)) ? dst[h + q] : 0.0;
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
+        for (int q = 0; q < HB; ++q)
           if (full || col0 + h + q < a.nout) dst[h + q] = old[q] + f32_to_f64(v[h + q]);
       }
     } else {
@@ -410,16 +418,16 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     const size_t cs64 = (size_t)a.nx * a.ny;
     const size_t o0 = (size_t)i + (size_t)a.nx * j + (size_t)col0 * cs64;
 #pragma unroll
-    for (int h = 0; h < 32; h += 16) {
-      float oh[16], ol[16];
+    for (int h = 0; h < 32; h += HB) {
+      float oh[HB], ol[HB];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < HB; ++q) {
         const bool ok = full || col0 + h + q < a.nout;
         oh[q] = (MODE != OUT_DF_STORE && ok) ? a.df_hi[d0 + (size_t)(h + q) * dcs] : 0.f;
         ol[q] = (MODE != OUT_DF_STORE && ok) ? a.df_lo[d0 + (size_t)(h + q) * dcs] : 0.f;
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < HB; ++q) {
         if (!(full || col0 + h + q < a.nout)) continue;
         const size_t d = d0 + (size_t)(h + q) * dcs;
         if (MODE == OUT_DF_STORE) {
@@ -450,13 +458,13 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     double* p = a.out64 + base + (size_t)col0 * cs64;
     // Loads first, 16 at a time (see the x pass).
 #pragma unroll
-    for (int h = 0; h < 32; h += 16) {
-      double old[16];
+    for (int h = 0; h < 32; h += HB) {
+      double old[HB];
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
+      for (int q = 0; q < HB; ++q)
         old[q] = (MODE == OUT_F64_ACCUM && (full || col0 + h + q < a.nout)) ? p[(size_t)(h + q) * cs64] : 0.0;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
+      for (int q = 0; q < HB; ++q)
         if (full || col0 + h + q < a.nout) p[(size_t)(h + q) * cs64] = old[q] + f32_to_f64(v[h + q]);
     }
   } else {
@@ -494,7 +502,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
 // bf16 operands (rounding ~2^-17, which dominates) a.kc covers the whole K and
 // each TMEM buffer holds one finished tile as before.
 template <int PASS, int MODE, int CL, int NP, int FMT>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+__global__ void __launch_bounds__(num_threads(MODE), 1)
     mode_product_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                                const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                                const TcArgs a) {
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), CL); }
-    for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), EPI_WARPS); }
+    for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), epi_warps(MODE)); }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -647,12 +655,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     mma_commit(drain_bar);
     mbar_wait(drain_bar, 0, nullptr);
   } else if (warp >= 2) {
-    // ------------------------------------------------ epilogue (EPI_WARPS warps)
+    // ------------------------------------------------ epilogue (epi_warps(MODE) warps)
     // Warp w reads TMEM lane quadrant w % 4 (hardware rule) and one of
-    // EPI_WARPS/4 column slices of the tile.
+    // epi_warps(MODE)/4 column slices of the tile.
     const int quad = warp & 3;
     const int slice = (warp - 2) >> 2;
-    constexpr int COLS = BN / (EPI_WARPS / 4);
+    constexpr int COLS = BN / (epi_warps(MODE) / 4);
     // F16X3: scales from the state the previous kernels left (every CTA
     // computes the same values; one thread publishes this pass's exponent).
     float sc_in = 1.f, sc_out = 1.f;
@@ -808,7 +816,7 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(CLUSTER * (num_sms / CLUSTER));
-      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.blockDim = dim3(num_threads(MODE));
       cfg.dynamicSmemBytes = SMEM_BYTES;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
@@ -829,7 +837,7 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)(clusters * CLUSTER));
-  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.blockDim = dim3(num_threads(MODE));
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
   cfg.attrs = attr;
