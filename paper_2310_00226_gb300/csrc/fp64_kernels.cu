@@ -630,19 +630,31 @@ __global__ void zero_pads_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int nx, i
 }
 
 // FP64 (dense, pitch nx) -> bf16 hi + lo (pitch Px, zero pads):
-// hi = bf16(x), lo = bf16(x - hi), x rounded to FP32 first.
+// hi = bf16(x), lo = bf16(x - hi), x rounded to FP32 first.  Blocks walk the
+// (j, l) lines; a lane converts 4 consecutive entries and writes them as one
+// 8-byte store per array (rows of pitch Px, a multiple of 16, are aligned).
 __global__ void __launch_bounds__(256) split_kernel(const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, int nx,
                                                     int Px, long long lines) {
-  const long long total = lines * Px;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long line = e / Px;
-    const int i = (int)(e - line * Px);
-    float x = 0.f;
-    if (i < nx) x = (float)in[line * nx + i];
-    const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
-    hi[e] = h16;
-    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h16));
+  const int chunks = Px >> 2;
+  for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
+    const double* row = in + line * nx;
+    uint2* hrow = reinterpret_cast<uint2*>(hi + line * Px);
+    uint2* lrow = reinterpret_cast<uint2*>(lo + line * Px);
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+      uint32_t hw[2], lw[2];
+#pragma unroll
+      for (int p = 0; p < 4; p += 2) {
+        const int i = 4 * c + p;
+        const float x0 = i < nx ? f64_to_f32_rn(row[i]) : 0.f, x1 = i + 1 < nx ? f64_to_f32_rn(row[i + 1]) : 0.f;
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+        hw[p / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lw[p / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      hrow[c] = make_uint2(hw[0], hw[1]);
+      lrow[c] = make_uint2(lw[0], lw[1]);
+    }
   }
 }
 
@@ -792,7 +804,7 @@ __global__ void __launch_bounds__(256) split_f16_kernel(const void* in, __half* 
     const long long line = idx / Px;
     const int i = (int)(idx - line * Px);
     float x = 0.f;
-    if (i < nx) x = IN64 ? (float)static_cast<const double*>(in)[line * nx + i] : static_cast<const float*>(in)[idx];
+    if (i < nx) x = IN64 ? f64_to_f32_rn(static_cast<const double*>(in)[line * nx + i]) : static_cast<const float*>(in)[idx];
     x *= sc;
     const __half h = __float2half_rn(x);
     hi[idx] = h;
@@ -816,7 +828,8 @@ cudaError_t launch_split_f16(const Geom& g, const void* in, bool in_f64, __half*
 
 cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
   const long long lines = (long long)g.ny * g.nz;
-  split_kernel<<<grid_for(lines * g.Px, 256), 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines);
+  const long long blocks = lines < 152LL * 16 ? (lines < 1 ? 1 : lines) : 152LL * 16;
+  split_kernel<<<(int)blocks, 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines);
   return cudaGetLastError();
 }
 

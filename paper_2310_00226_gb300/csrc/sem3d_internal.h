@@ -14,6 +14,27 @@
 
 namespace sem3d {
 
+#ifdef __CUDACC__
+// FP64 -> FP32 with round-to-nearest-even, in integer arithmetic from the
+// IEEE 754 binary64/binary32 formats (the hardware conversion runs on the FP64
+// pipe, 1/64 of the FP32 rate on this GPU).  Results in the FP32 normal range
+// (and overflow to infinity) are formed here; the rare subnormal results and
+// NaN inputs take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;  // biased FP32 exponent
+  if (e <= 0 || ((b >> 52) & 0x7FF) == 0x7FF) return __double2float_rn(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned int r = ((unsigned int)e << 23) | (unsigned int)(m >> 29);  // truncated
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull), half = 0x10000000u;
+  r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;  // a carry rounds into the exponent
+  return __uint_as_float(sign | r);
+}
+#endif
+
+
 // ---------------------------------------------------------------- host setup
 
 // 1D data of one axis of degree k on [0, L]: with homogeneous Dirichlet data
