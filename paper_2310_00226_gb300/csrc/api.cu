@@ -425,7 +425,8 @@ sem3d_status sem3d_tuned_config(sem3d_handle h, int axis, int* config) {
 
 sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode) {
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
-  if (mode != SEM3D_RESIDUAL_FP64 && mode != SEM3D_RESIDUAL_MIXED) return fail(SEM3D_ERR_INVALID_ARG, "unknown mode");
+  if (mode != SEM3D_RESIDUAL_FP64 && mode != SEM3D_RESIDUAL_MIXED && mode != SEM3D_RESIDUAL_DF)
+    return fail(SEM3D_ERR_INVALID_ARG, "unknown mode");
   h->residual = mode;
   return SEM3D_OK;
 }
@@ -487,10 +488,14 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
     DfBuffers D{reinterpret_cast<float*>(w + 6 * Ns), reinterpret_cast<float*>(w + 6 * Ns + Nf)};
     const DfBuffers none{nullptr, nullptr};
     const int sw = h->sweeps;
-    // Mixed residuals: sweeps 1 .. sw-1 in double-FP32 with the solution held
-    // as a double-FP32 pair, the last sweep in FP64 on the FP64 solution.
-    const bool mixed = h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2 && h->k <= 8 && h->g.bc == 0 &&
-                       (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_F16X3);
+    // Double-FP32 sweeps (the solution held as a double-FP32 pair between
+    // them): SEM3D_RESIDUAL_MIXED runs sweeps 1 .. sw-1 so and the last one in
+    // FP64 on the FP64 solution; SEM3D_RESIDUAL_DF runs every sweep so.
+    const bool df_ok = h->k <= 8 && h->g.bc == 0 && (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_F16X3);
+    const int ndf = !df_ok ? 0
+                           : (h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2) ? sw - 1
+                           : (h->residual == SEM3D_RESIDUAL_DF) ? sw : 0;
+    const bool mixed = ndf > 0;
     const bool f16 = h->prec == SEM3D_F16X3;
     // F16X3: the residual is written as FP32 into S1's storage (4 bytes per
     // entry at pitch Px fit in its hi + lo arrays) and then split with a
@@ -513,7 +518,7 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
       if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_STORE, none, s)) != SEM3D_OK) return st;
     } else {
       if ((st = solve_once_bf16x3(h, S0, S1, nullptr, EPI_DF_STORE, D, s)) != SEM3D_OK) return st;
-      for (int q = 1; q < sw; ++q) {
+      for (int q = 1; q <= ndf; ++q) {
         if (f16) {
           if ((st = reset_scales()) != SEM3D_OK) return st;
           LAUNCH(h, K_STENCIL, 1, s, launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16));
@@ -524,13 +529,13 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
           const int df_launches = (h->k == 1 || h->k == 2 || h->k == 4 || h->g.Px == h->g.nx) ? 1 : 2;
           LAUNCH(h, K_STENCIL, df_launches, s, launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
         }
-        const bool last_df = (q == sw - 1);
+        const bool last_df = (q == ndf);
         if ((st = solve_once_bf16x3(h, S0, S1, last_df ? u : nullptr, last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, D,
                                     s)) != SEM3D_OK)
           return st;
       }
     }
-    for (int q = mixed ? sw - 1 : 0; q < sw; ++q) {
+    for (int q = ndf; q < sw; ++q) {
       if (f16) {
         if ((st = reset_scales()) != SEM3D_OK) return st;
         LAUNCH(h, K_STENCIL, 1, s, launch_stencil_f32out(h->g, h->k, h->dev, u, f, r32, h->d_f16, s));

@@ -170,7 +170,7 @@ class Plan:
     def set_precision(self, precision: str = "fp64", sweeps: int = 1):
         _check(lib().sem3d_set_precision(self._h, PRECISIONS[precision], int(sweeps)), "sem3d_set_precision")
 
-    RESIDUALS = {"fp64": 0, "mixed": 1}
+    RESIDUALS = {"fp64": 0, "mixed": 1, "df": 2}
 
     def set_residual(self, mode: str = "mixed"):
         _check(lib().sem3d_set_residual(self._h, self.RESIDUALS[mode]), "sem3d_set_residual")

@@ -110,9 +110,12 @@ def test_bf16x3_solve_matches_oracle(sem3d, i):
 
 
 @pytest.mark.parametrize("i", [2, 3, 5])
-@pytest.mark.parametrize("residual,sweeps", [("fp64", 3), ("mixed", 2), ("mixed", 4)])
+@pytest.mark.parametrize("residual,sweeps", [("fp64", 3), ("mixed", 2), ("mixed", 4), ("df", 1), ("df", 3)])
 def test_bf16x3_residual_modes(sem3d, i, residual, sweeps):
     # Mixed: double-FP32 residuals for all sweeps but the last, which is FP64.
+    # df: every residual in double-FP32 (~48 bits): its 2^-48 error, amplified
+    # by the conditioning of the operator, leaves ~2e-12 at n=383 (measured):
+    # bound 1e-11, the reason the library's default keeps the last sweep FP64.
     n3, k, L3, c, (sx, sy, sz), F = _case(i)
     ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
     with sem3d.Plan(*n3, k, L3, c) as p:
@@ -123,9 +126,12 @@ def test_bf16x3_residual_modes(sem3d, i, residual, sweeps):
         p.solve(f, u)
         p.sync_check()
         err = _rel(u.cpu().numpy(), ref)
-    # two sweeps reach ~1e-11 at most sizes: the bound is the contraction
-    # of two BF16x3 corrections; three or more reach rounding level.
-    assert err < (1e-12 if sweeps >= 3 else 1e-9), err
+    # one or two sweeps: the contraction of one or two BF16x3 corrections;
+    # three or more reach rounding level.
+    bound = 1e-12 if sweeps >= 3 else (1e-9 if sweeps == 2 else 1e-6)
+    if residual == "df":
+        bound = max(bound, 1e-11)
+    assert err < bound, err
 
 
 @pytest.mark.parametrize("i", [2, 4, 5])
