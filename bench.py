@@ -417,9 +417,10 @@ def run_workload(args, rank: int):
         rng = np.random.Generator(np.random.PCG64(20231001))
         phi0 = torch.from_numpy(rng.uniform(-0.05, 0.05, (n, n, n))).cuda()
         res = {}
-        for prec in ("bf16x3", "fp32"):
+        tiers = ["bf16x3", "fp32"] + (["fp64"] if args.ch_fp64_steps > 0 else [])
+        for prec in tiers:
             p.set_precision(prec, 0)
-            steps = args.ch_steps if prec == "bf16x3" else max(1, args.ch_steps // 10)
+            steps = {"bf16x3": args.ch_steps, "fp32": max(1, args.ch_steps // 10), "fp64": args.ch_fp64_steps}[prec]
             pm, pn = phi0.clone(), phi0.clone()
             p.ch_run(pm, pn, 3, 0.05, 1.0, 1e-4, 2.0, stream)  # warm-up
             torch.cuda.synchronize()
@@ -440,14 +441,16 @@ def run_workload(args, rank: int):
         f = torch.ones_like(V)
         u = torch.empty_like(V)
         res = {}
-        for prec, sweeps in (("bf16x3", 0), ("bf16x3", 1)):
+        variants = [("bf16x3", 0), ("bf16x3", 1)] + ([("fp64", 0)] if args.pcg_fp64 else [])
+        for prec, sweeps in variants:
             p.set_precision(prec, sweeps)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             it, rr = p.pcg(V, f, u, rtol=1e-10, maxit=200, stream=stream)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3
-            res[f"{prec}_sweeps{sweeps}"] = {"ms": ms, "iterations": it, "relres": rr, "ms_per_iteration": ms / it}
+            res[f"{prec}_sweeps{sweeps}"] = {"ms": ms, "iterations": it, "relres": rr, "ms_per_iteration": ms / it,
+                                             "u_max": float(u.abs().max())}
         line.update({"metric": f"Schroedinger -Lap u + 100|x-1/2|^2 u = 1, Q^4 n={n} ({n**3:.3g} DoF), PCG to 1e-10: s",
                      "value": min(r["ms"] for r in res.values()) / 1e3, "unit": "s", "higher_is_better": False,
                      "preconditioner": res})
@@ -478,6 +481,10 @@ def main():
     ap.add_argument("--workload-n", type=int, default=None,
                     help="grid size of the ch (default 511) or pcg (default 1023) workload, for small profiling runs")
     ap.add_argument("--batch-count", type=int, default=64, help="problems in the batched workload")
+    ap.add_argument("--ch-fp64-steps", type=int, default=0,
+                    help="also time this many Cahn-Hilliard steps in the FP64 tier (~1.2 s per step at n=511)")
+    ap.add_argument("--pcg-fp64", action="store_true",
+                    help="also run the PCG with the FP64 (DMMA) preconditioner (~13 s per iteration at n=1023)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
