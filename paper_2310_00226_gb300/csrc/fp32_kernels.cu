@@ -102,13 +102,7 @@ __device__ __forceinline__ void f32_tile(const F32Pass& p, long long bx, int by,
 #pragma unroll
     for (int it = 0; it < C::LA; ++it) {
       const int t = t0 + akk[it];
-      if (abase[it] >= 0 && t < p.n) {
-        const TIN x = in[abase[it] + (long long)t * p.sm];
-        if constexpr (sizeof(TIN) == 8) ra[it] = f64_to_f32_rn(x);  // integer path: keeps the FP64 pipe free
-        else ra[it] = x;
-      } else {
-        ra[it] = 0.f;
-      }
+      ra[it] = (abase[it] >= 0 && t < p.n) ? (float)in[abase[it] + (long long)t * p.sm] : 0.f;
     }
 #pragma unroll
     for (int it = 0; it < C::LW; ++it) {

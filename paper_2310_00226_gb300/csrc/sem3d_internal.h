@@ -15,22 +15,33 @@
 namespace sem3d {
 
 #ifdef __CUDACC__
-// FP64 -> FP32 with round-to-nearest-even, in integer arithmetic from the
-// IEEE 754 binary64/binary32 formats (the hardware conversion runs on the FP64
-// pipe, 1/64 of the FP32 rate on this GPU).  Results in the FP32 normal range
-// (and overflow to infinity) are formed here; the rare subnormal results and
-// NaN inputs take the hardware conversion.
+// FP64 -> FP32 with round-to-nearest-even, entirely in integer arithmetic
+// from the IEEE 754 binary64/binary32 formats (the hardware conversion runs on
+// the FP64 pipe, 1/64 of the FP32 rate on this GPU).  Covers normal and
+// subnormal results, overflow to infinity, zeros, infinities and NaN (quieted).
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;  // biased FP32 exponent
-  if (e <= 0 || ((b >> 52) & 0x7FF) == 0x7FF) return __double2float_rn(x);
   const unsigned int sign = (unsigned int)(b >> 63) << 31;
-  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const int ex = (int)((b >> 52) & 0x7FF);
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  unsigned int r = ((unsigned int)e << 23) | (unsigned int)(m >> 29);  // truncated
-  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull), half = 0x10000000u;
-  r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;  // a carry rounds into the exponent
-  return __uint_as_float(sign | r);
+  if (ex == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u | (unsigned int)(m >> 29) : 0u));
+  const int e = ex - 1023 + 127;  // biased FP32 exponent
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  if (e >= 1) {
+    unsigned int r = ((unsigned int)e << 23) | (unsigned int)(m >> 29);  // truncated
+    const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull), half = 0x10000000u;
+    r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;  // a carry rounds into the exponent
+    return __uint_as_float(sign | r);
+  }
+  // Subnormal (or zero) result: significand 1.m (53 bits) scaled to units of
+  // 2^-149, i.e. shifted right by s = 30 - e >= 30 bits, then rounded.
+  if (ex == 0) return __uint_as_float(sign);  // FP64 zero or subnormal: below half of 2^-149
+  const int sh = 30 - e;
+  if (sh > 54) return __uint_as_float(sign);
+  const unsigned long long sig = m | (1ull << 52);
+  const unsigned int q = (unsigned int)(sig >> sh);
+  const unsigned long long rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  return __uint_as_float(sign | (q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u)));
 }
 #endif
 
