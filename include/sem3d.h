@@ -278,6 +278,15 @@ sem3d_status sem3d_tuned_config(sem3d_handle h, int axis, int* config);
  * the next pin; sem3d_set_precision does not re-measure a known shape). */
 sem3d_status sem3d_set_tuned_config(sem3d_handle h, int axis, int config);
 
+/* Failure-detection testing (no counterpart in the paper).  The next
+ * `launches` tensor-core kernel launches of the process (any plan) issue no
+ * operand loads: their bounded waits (1 s each, on mbarriers that nothing then
+ * arms) expire, the kernels record SEM3D_ERR_TIMEOUT, release their tensor
+ * memory and return, and the next sem3d_sync_check reports the timeout.  No
+ * GPU fault is raised; the plan and the CUDA context stay usable, and later
+ * solves are correct.  0 cancels.  launches in [0, 64]; h only validates. */
+sem3d_status sem3d_inject_stall(sem3d_handle h, int launches);
+
 /* Total number of kernels this plan has launched since sem3d_setup. */
 sem3d_status sem3d_launch_count(sem3d_handle h, unsigned long long* count);
 

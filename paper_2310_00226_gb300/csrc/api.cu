@@ -408,6 +408,13 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweep
   return SEM3D_OK;
 }
 
+sem3d_status sem3d_inject_stall(sem3d_handle h, int launches) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  if (launches < 0 || launches > 64) return fail(SEM3D_ERR_INVALID_ARG, "launches must be in [0, 64]");
+  tc_inject_stall(launches);
+  return SEM3D_OK;
+}
+
 sem3d_status sem3d_set_tuned_config(sem3d_handle h, int axis, int config) {
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
   if (axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "axis must be 0, 1 or 2");

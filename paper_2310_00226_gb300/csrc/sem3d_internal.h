@@ -206,6 +206,9 @@ struct TcPassPlan;
 // One BF16x3 mode product along `axis` reading the split array `in` and
 // writing either the split array `out` (EPI_STORE / EPI_DIV) or the FP64
 // dense n-pitch array out64 (EPI_STORE / EPI_ACCUM).
+// Failure-detection testing: the next `launches` tensor-core launches of the
+// process issue no operand loads, so their bounded waits expire.
+void tc_inject_stall(int launches);
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,

@@ -32,6 +32,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 namespace sem3d {
@@ -244,6 +245,7 @@ struct TcArgs {
   F16State* st;
   int pin, pout, eW;
   float normW, div_bound;
+  int stall;           // failure-detection test: the producer issues no loads, so the waits expire
 };
 
 // Output modes of the epilogue.  The DF modes (y and z passes only) keep the
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
     // ------------------------------------------------ TMA producer
     int it = 0;
     bool ok = true;
-    for (int ct = cid; ct < total_ct && ok; ct += ncl) {
+    for (int ct = cid; ct < total_ct && ok && !a.stall; ct += ncl) {
       const int b = ct / tiles_per_batch;
       const int rem = ct - b * tiles_per_batch;
       const int mg = rem / a.n_tiles, nt = rem - mg * a.n_tiles;
@@ -895,6 +897,11 @@ cudaError_t launch_tc_mode(int mode, int nprod, int fmt, const CUtensorMap& a0, 
 static constexpr CUtensorMapSwizzle SWZ_K = CU_TENSOR_MAP_SWIZZLE_64B;
 static constexpr CUtensorMapSwizzle SWZ_MN = CU_TENSOR_MAP_SWIZZLE_128B;
 
+// Launches that still have to run with the producer stalled (sem3d_inject_stall).
+std::atomic<int> g_stall_launches{0};
+
+void tc_inject_stall(int launches) { g_stall_launches.store(launches); }
+
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
@@ -913,6 +920,12 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   }
   if (out64 && epi == EPI_DIV) return cudaErrorInvalidValue;
   TcArgs a{};
+  {
+    int left = g_stall_launches.load();
+    while (left > 0 && !g_stall_launches.compare_exchange_weak(left, left - 1)) {
+    }
+    a.stall = left > 0 ? 1 : 0;
+  }
   a.df_hi = df.hi;
   a.df_lo = df.lo;
   if (f16) {

@@ -45,6 +45,7 @@ EXPORTS = (
     "sem3d_launch_count",
     "sem3d_tuned_config",
     "sem3d_set_tuned_config",
+    "sem3d_inject_stall",
     "sem3d_solve_fp64_static",
     "sem3d_destroy",
     "sem3d_last_error",
@@ -95,6 +96,7 @@ def lib() -> ctypes.CDLL:
     L.sem3d_launch_count.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]
     L.sem3d_tuned_config.argtypes = [c_void_p, c_int, ctypes.POINTER(c_int)]
     L.sem3d_set_tuned_config.argtypes = [c_void_p, c_int, c_int]
+    L.sem3d_inject_stall.argtypes = [c_void_p, c_int]
     L.sem3d_solve_fp64_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_destroy.argtypes = [c_void_p]
     L.sem3d_last_error.restype = ctypes.c_char_p

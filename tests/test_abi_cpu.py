@@ -64,6 +64,7 @@ def test_setup_argument_validation(L):
     assert b"c must be > 0" in L.sem3d_last_error()
     assert L.sem3d_setup_bc(7, 7, 7, 2, 1.0, 1.0, 1.0, 1.0, 2, ctypes.byref(h)) == 1
     assert L.sem3d_tuned_config(None, 0, None) == 1
+    assert L.sem3d_inject_stall(None, 1) == 1
     assert L.sem3d_set_tuned_config(None, 0, 0) == 1
     assert L.sem3d_destroy(None) == 0
 

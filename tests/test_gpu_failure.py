@@ -1,0 +1,65 @@
+"""Failure detection on the GPU without a GPU fault.
+
+Every wait inside the tensor-core kernel is bounded (1 s on the global timer)
+and records SEM3D_ERR_TIMEOUT in the plan's device error word when it expires.
+sem3d_inject_stall makes the next tensor-core launch issue no operand loads, so
+the MMA warp waits on a barrier that nothing arms: the wait must expire, the
+kernel must return (releasing its tensor memory), sem3d_sync_check must report
+the timeout, and the same plan must then solve correctly.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import refined_solve, sem_1d
+from paper_2310_00226_gb300.inputs import random_rhs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TIMEOUT = 5  # SEM3D_ERR_TIMEOUT
+
+
+@pytest.fixture(scope="module")
+def sem3d():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2310_00226_gb300 import sem3d as mod
+    mod.lib()
+    return mod
+
+
+@pytest.mark.parametrize("tier", ["bf16x3", "f16x3"])
+def test_expired_wait_is_reported_and_the_plan_recovers(sem3d, tier):
+    n3, k = (63, 31, 47), 2
+    axes = [sem_1d(k, (n + 1) // k, 0.0, 1.0) for n in n3]
+    F = random_rhs(*n3, seed=17)
+    ref = refined_solve(F, *axes, 1.0, sweeps=1)
+    with sem3d.Plan(*n3, k, (1.0, 1.0, 1.0), 1.0) as p:
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.set_precision(tier, 0)
+        p.solve(f, u)              # warm-up: workspace and kernels loaded
+        p.sync_check()
+        assert sem3d.lib().sem3d_inject_stall(p._h, 1) == 0
+        p.solve(f, u)              # the first pass's producer stalls
+        with pytest.raises(sem3d.Sem3dError) as exc:
+            p.sync_check()
+        assert exc.value.status == TIMEOUT
+        # the error word was cleared and the context is usable: a normal refined solve
+        p.set_precision(tier, 3)
+        p.solve(f, u)
+        p.sync_check()
+        err = float(np.abs(u.cpu().numpy() - ref).max() / np.abs(ref).max())
+        assert err < 1e-12, err
+
+
+def test_injection_is_consumed_once(sem3d):
+    with sem3d.Plan(15, 15, 15, 2, (1.0, 1.0, 1.0), 1.0) as p:
+        p.set_precision("bf16x3", 1)
+        f = torch.ones(15 ** 3, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(f)
+        assert sem3d.lib().sem3d_inject_stall(p._h, 1) == 0
+        assert sem3d.lib().sem3d_inject_stall(p._h, 0) == 0   # cancelled before any launch
+        p.solve(f, u)
+        p.sync_check()                                        # no timeout
