@@ -265,3 +265,27 @@ def test_solve_is_repeatable_and_stream_ordered(sem3d):
             p.solve(f, u2, stream=s)
         p.sync_check(stream=s)
         assert torch.equal(u1, u2)
+
+
+@pytest.mark.parametrize("tier,sweeps", [("bf16x3", 3), ("f16x3", 3), ("fp32", 2), ("fp64", 1)])
+def test_solve_captures_into_a_cuda_graph(sem3d, tier, sweeps):
+    # With a fixed sweep count the solve makes no host synchronisation, so it can
+    # be captured in a CUDA graph; replays must equal the eager result bit for bit.
+    n3, k, L3, c, (sx, sy, sz), F = _case(3)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        p.set_precision(tier, sweeps)
+        s = torch.cuda.Stream()
+        f = torch.from_numpy(F).cuda()
+        u_eager = torch.empty_like(f)
+        u_graph = torch.full_like(f, float("nan"))
+        with torch.cuda.stream(s):
+            p.solve(f, u_eager, stream=s)   # also allocates the workspace before capture
+        p.sync_check(stream=s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.solve(f, u_graph, stream=s)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        p.sync_check(stream=s)
+        assert torch.equal(u_graph, u_eager)
