@@ -46,7 +46,13 @@ constexpr int STAGES = 4;
 constexpr int A_TILE_BYTES = BM * BK * 2;  // 8 KB
 constexpr int B_TILE_BYTES = BN * BK * 2;  // 16 KB
 constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+// x-pass split outputs are staged per epilogue warp (32 rows x 64 bytes, rows
+// padded to 80 bytes so that 16-byte accesses of 8 lanes hit distinct banks)
+// and written back row-contiguously; see epilogue_chunk.
+constexpr int XSTAGE_ROW = 80, XSTAGE_BYTES = 32 * XSTAGE_ROW;
+__host__ __device__ constexpr int smem_bytes(int pass) {
+  return STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + (pass == 0 ? 8 * XSTAGE_BYTES : 0);
+}
 constexpr int TMEM_COLS = 2 * BN;  // 512
 // Epilogue warps: two per TMEM lane quadrant for the split-bf16 outputs; four
 // for the outputs that read and write FP64 / double-FP32 solution arrays
@@ -317,7 +323,7 @@ __device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
 // value -> stored split value (2^e_out, 1 for bf16); vmax: running max |true|.
 template <int PASS, int MODE, int NP, int FMT>
 __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32],
-                                               float sc_in, float sc_out, float& vmax) {
+                                               float sc_in, float sc_out, float& vmax, uint8_t* xstage) {
   const bool full = col0 + 32 <= a.nout;
   // Read-modify-write batches: loads of HB elements are issued before their
   // stores (independent, but the compiler cannot prove it through one
@@ -328,9 +334,11 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     for (int q = 0; q < 32; ++q) v[q] *= sc_in;
   }
   if (PASS == 0) {
-    if (row >= a.rows) return;
+    // Split outputs are stored by the whole warp (staged); the other outputs per lane.
+    if (row >= a.rows && !(MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) return;
     if (MODE == OUT_DIV_SPLIT) {
-      const int j = row % a.ny, l = row / a.ny;
+      const int rr = row < a.rows ? row : 0;  // rows past the end (not stored) read valid entries
+      const int j = rr % a.ny, l = rr / a.ny;
       const float s = __ldg(a.lamy + j) + __ldg(a.lamz + l) + a.c;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
@@ -342,7 +350,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
     if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        if (full || col0 + q < a.nout) vmax = fmaxf(vmax, fabsf(v[q]));
+        if (row < a.rows && (full || col0 + q < a.nout)) vmax = fmaxf(vmax, fabsf(v[q]));
         v[q] *= sc_out;
       }
     }
@@ -362,18 +370,36 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
           if (full || col0 + h + q < a.nout) dst[h + q] = old[q] + f32_to_f64(v[h + q]);
       }
     } else {
-      __nv_bfloat16* dh = a.out_hi + (size_t)row * a.Px + col0;
-      __nv_bfloat16* dl = a.out_lo + (size_t)row * a.Px + col0;
+      // Each lane holds 32 consecutive outputs of its own row (line).  Written
+      // directly, every 16-byte store of the warp would touch 32 rows; instead
+      // the warp stages its 32 x 32 block in shared memory and writes it back
+      // with 4 lanes per row: each store instruction covers 8 full 64-byte row
+      // segments.  All 32 lanes take part (rows past the end are not stored).
+      const int lane = threadIdx.x & 31;
+      const int row0 = row - lane;
+      uint4 hh[4], ll[4];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        if (col0 + 8 * g + 8 > a.Px) break;  // Px is a multiple of 16
-        uint4 hh, ll;
-        split_any<FMT>(v[8 * g + 0], v[8 * g + 1], hh.x, ll.x);
-        split_any<FMT>(v[8 * g + 2], v[8 * g + 3], hh.y, ll.y);
-        split_any<FMT>(v[8 * g + 4], v[8 * g + 5], hh.z, ll.z);
-        split_any<FMT>(v[8 * g + 6], v[8 * g + 7], hh.w, ll.w);
-        *reinterpret_cast<uint4*>(dh + 8 * g) = hh;
-        if (NP == 3) *reinterpret_cast<uint4*>(dl + 8 * g) = ll;
+        split_any<FMT>(v[8 * g + 0], v[8 * g + 1], hh[g].x, ll[g].x);
+        split_any<FMT>(v[8 * g + 2], v[8 * g + 3], hh[g].y, ll[g].y);
+        split_any<FMT>(v[8 * g + 4], v[8 * g + 5], hh[g].z, ll[g].z);
+        split_any<FMT>(v[8 * g + 6], v[8 * g + 7], hh[g].w, ll[g].w);
+      }
+#pragma unroll
+      for (int part = 0; part < (NP == 3 ? 2 : 1); ++part) {
+        __nv_bfloat16* dst = part == 0 ? a.out_hi : a.out_lo;
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          *reinterpret_cast<uint4*>(xstage + lane * XSTAGE_ROW + 16 * g) = part == 0 ? hh[g] : ll[g];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = 8 * k + (lane >> 2), seg = lane & 3;
+          const uint4 val = *reinterpret_cast<const uint4*>(xstage + r * XSTAGE_ROW + 16 * seg);
+          if (row0 + r < a.rows && col0 + 8 * seg + 8 <= a.Px)  // Px is a multiple of 16
+            *reinterpret_cast<uint4*>(dst + (size_t)(row0 + r) * a.Px + col0 + 8 * seg) = val;
+        }
+        __syncwarp();
       }
     }
     return;
@@ -662,6 +688,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
     // epi_warps(MODE)/4 column slices of the tile.
     const int quad = warp & 3;
     const int slice = (warp - 2) >> 2;
+    uint8_t* xstage = PASS == 0 ? smem + STAGES * STAGE_BYTES + 256 + (warp - 2) * XSTAGE_BYTES : nullptr;
     constexpr int COLS = BN / (epi_warps(MODE) / 4);
     // F16X3: scales from the state the previous kernels left (every CTA
     // computes the same values; one thread publishes this pass's exponent).
@@ -718,7 +745,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
           if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(prev * BN + ch * 32), v);
-          epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax);
+          epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax, xstage);
         }
         tc_fence_before();
         __syncwarp();
@@ -734,7 +761,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
           if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
           float v[32];
           tmem_ld32(lane_addr + (uint32_t)(buf * BN + ch * 32), v);
-          epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax);
+          epilogue_chunk<PASS, MODE, NP, FMT>(a, row, col0, b, v, sc_in, sc_out, vmax, xstage);
         }
         tc_fence_before();
         __syncwarp();
@@ -808,7 +835,7 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
   auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER, NP, FMT>;
   static int max_clusters = 0;  // per instantiation: co-resident clusters of CLUSTER CTAs
   if (max_clusters == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PASS));
     if (e != cudaSuccess) return e;
     if (CLUSTER > 1) {
       cudaLaunchConfig_t cfg = {};
@@ -819,7 +846,7 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
       attr[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(CLUSTER * (num_sms / CLUSTER));
       cfg.blockDim = dim3(num_threads(MODE));
-      cfg.dynamicSmemBytes = SMEM_BYTES;
+      cfg.dynamicSmemBytes = smem_bytes(PASS);
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       int n = 0;
@@ -840,7 +867,7 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)(clusters * CLUSTER));
   cfg.blockDim = dim3(num_threads(MODE));
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.dynamicSmemBytes = smem_bytes(PASS);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
