@@ -150,6 +150,24 @@ sem3d_status sem3d_set_workspace(sem3d_handle h, void* dptr, size_t bytes);
  * Enqueued on `stream`; no host synchronisation. */
 sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* stream);
 
+/* sem3d_solve with the data in HOST memory, pipelined across calls.  Each
+ * call copies f_host to the device, solves in the plan's mode on `stream` and
+ * copies the result to u_host, all asynchronously: the copies use the plan's
+ * own host->device and device->host streams and two device (f, u) pairs used in
+ * turn, so consecutive calls overlap one call's copies with another's solve
+ * (the copy engines run both directions at once).  The first call allocates the
+ * two pairs (4 * nx*ny*nz doubles).  f_host and u_host should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for the copies to be asynchronous; f_host
+ * must stay unchanged and u_host unread until sem3d_solve_host_wait's stream
+ * work has completed.  Calls on one plan must come from one host thread. */
+sem3d_status sem3d_solve_host(sem3d_handle h, const double* f_host, double* u_host, void* stream);
+
+/* Make `stream` wait for the device->host copies of every earlier
+ * sem3d_solve_host call of this plan (the results are in host memory once the
+ * stream's work up to this point has completed; synchronise it or record an
+ * event). */
+sem3d_status sem3d_solve_host_wait(sem3d_handle h, void* stream);
+
 /* Many independent solves (the benchmark spec's batched workload; each problem is
  * Section 2.4's solve on its own box, grid, degree and shift).
  *   count : number of problems, 1 <= count <= 1024.

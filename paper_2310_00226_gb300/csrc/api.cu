@@ -85,6 +85,15 @@ struct sem3d_plan {
   PcgScalars* pcg_sc = nullptr;
   double* ch_buf = nullptr;  // third phi buffer of sem3d_ch_run
   cudaStream_t pcg_stream = nullptr;
+  // sem3d_solve_host: two device (f, u) pairs used in turn, copy streams and events.
+  struct HostIo {
+    double* f[2] = {nullptr, nullptr};
+    double* u[2] = {nullptr, nullptr};
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t copied_in[2] = {nullptr, nullptr}, solved[2] = {nullptr, nullptr}, copied_out[2] = {nullptr, nullptr};
+    bool used[2] = {false, false};
+    long long calls = 0;
+  } io;
   double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   long long prof_n[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
@@ -462,6 +471,51 @@ sem3d_status sem3d_solve(sem3d_handle h, const double* f, double* u, void* strea
   sem3d_status st = ensure_workspace(h);
   if (st != SEM3D_OK) return st;
   return run_solve(h, f, u, static_cast<cudaStream_t>(stream));
+}
+
+sem3d_status sem3d_solve_host(sem3d_handle h, const double* f_host, double* u_host, void* stream) {
+  if (!h || !f_host || !u_host) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  sem3d_status st = ensure_workspace(h);
+  if (st != SEM3D_OK) return st;
+  auto& io = h->io;
+  if (!io.h2d) {
+    for (int b = 0; b < 2; ++b) {
+      CUDA_TRY(cudaMalloc(&io.f[b], N * sizeof(double)));
+      CUDA_TRY(cudaMalloc(&io.u[b], N * sizeof(double)));
+      CUDA_TRY(cudaEventCreateWithFlags(&io.copied_in[b], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&io.solved[b], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&io.copied_out[b], cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaStreamCreateWithFlags(&io.h2d, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&io.d2h, cudaStreamNonBlocking));
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int b = (int)(io.calls++ & 1);
+  // f into buffer b once the solve that last read it is done.
+  if (io.used[b]) CUDA_TRY(cudaStreamWaitEvent(io.h2d, io.solved[b], 0));
+  CUDA_TRY(cudaMemcpyAsync(io.f[b], f_host, N * sizeof(double), cudaMemcpyHostToDevice, io.h2d));
+  CUDA_TRY(cudaEventRecord(io.copied_in[b], io.h2d));
+  // Solve on the caller's stream once f is in and u[b] has been copied out.
+  CUDA_TRY(cudaStreamWaitEvent(s, io.copied_in[b], 0));
+  if (io.used[b]) CUDA_TRY(cudaStreamWaitEvent(s, io.copied_out[b], 0));
+  if ((st = run_solve(h, io.f[b], io.u[b], s)) != SEM3D_OK) return st;
+  CUDA_TRY(cudaEventRecord(io.solved[b], s));
+  // u back to the host on the other copy stream.
+  CUDA_TRY(cudaStreamWaitEvent(io.d2h, io.solved[b], 0));
+  CUDA_TRY(cudaMemcpyAsync(u_host, io.u[b], N * sizeof(double), cudaMemcpyDeviceToHost, io.d2h));
+  CUDA_TRY(cudaEventRecord(io.copied_out[b], io.d2h));
+  io.used[b] = true;
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_solve_host_wait(sem3d_handle h, void* stream) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  auto& io = h->io;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int b = 0; b < 2; ++b)
+    if (io.used[b]) CUDA_TRY(cudaStreamWaitEvent(s, io.copied_out[b], 0));
+  return SEM3D_OK;
 }
 
 }  // extern "C"
@@ -1106,6 +1160,15 @@ sem3d_status sem3d_destroy(sem3d_handle h) {
   if (h->pcg_buf) cudaFree(h->pcg_buf);
   if (h->pcg_sc) cudaFree(h->pcg_sc);
   if (h->pcg_stream) cudaStreamDestroy(h->pcg_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (h->io.f[b]) cudaFree(h->io.f[b]);
+    if (h->io.u[b]) cudaFree(h->io.u[b]);
+    if (h->io.copied_in[b]) cudaEventDestroy(h->io.copied_in[b]);
+    if (h->io.solved[b]) cudaEventDestroy(h->io.solved[b]);
+    if (h->io.copied_out[b]) cudaEventDestroy(h->io.copied_out[b]);
+  }
+  if (h->io.h2d) cudaStreamDestroy(h->io.h2d);
+  if (h->io.d2h) cudaStreamDestroy(h->io.d2h);
   for (auto& ev : h->pending) { h->pool.push_back(ev.a); h->pool.push_back(ev.b); }
   for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
   if (h->ws && h->ws_owned) cudaFree(h->ws);

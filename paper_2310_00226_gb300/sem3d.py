@@ -31,6 +31,8 @@ EXPORTS = (
     "sem3d_workspace_size",
     "sem3d_set_workspace",
     "sem3d_solve",
+    "sem3d_solve_host",
+    "sem3d_solve_host_wait",
     "sem3d_solve_batched",
     "sem3d_apply",
     "sem3d_pcg",
@@ -78,6 +80,8 @@ def lib() -> ctypes.CDLL:
     L.sem3d_workspace_size.argtypes = [c_void_p, ctypes.POINTER(c_size_t)]
     L.sem3d_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
     L.sem3d_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.sem3d_solve_host_wait.argtypes = [c_void_p, c_void_p]
     L.sem3d_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_solve_batched.argtypes = [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                       ctypes.POINTER(c_void_p), c_void_p]
@@ -123,6 +127,15 @@ def _dev_ptr(t, n: int, name: str) -> int:
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return t.data_ptr()
+
+
+def _host_ptr(t, n: int, name: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CPU tensor (pinned for asynchronous copies)")
     if t.numel() != n:
         raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
     return t.data_ptr()
@@ -190,6 +203,16 @@ class Plan:
         _check(lib().sem3d_solve(self._h, ctypes.c_void_p(_dev_ptr(f, self.numel, "f")),
                                  ctypes.c_void_p(_dev_ptr(u, self.numel, "u")), ctypes.c_void_p(_stream_ptr(stream))),
                "sem3d_solve")
+
+    def solve_host(self, f_host, u_host, stream=None):
+        """Solve with host (pinned) tensors; pipelined with the plan's other solve_host calls.
+        Results are complete after solve_host_wait(stream) and a synchronisation of the stream."""
+        _check(lib().sem3d_solve_host(self._h, ctypes.c_void_p(_host_ptr(f_host, self.numel, "f_host")),
+                                      ctypes.c_void_p(_host_ptr(u_host, self.numel, "u_host")),
+                                      ctypes.c_void_p(_stream_ptr(stream))), "sem3d_solve_host")
+
+    def solve_host_wait(self, stream=None):
+        _check(lib().sem3d_solve_host_wait(self._h, ctypes.c_void_p(_stream_ptr(stream))), "sem3d_solve_host_wait")
 
     def apply(self, u, Au, stream=None):
         _check(lib().sem3d_apply(self._h, ctypes.c_void_p(_dev_ptr(u, self.numel, "u")),

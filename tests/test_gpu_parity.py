@@ -289,3 +289,26 @@ def test_solve_captures_into_a_cuda_graph(sem3d, tier, sweeps):
         torch.cuda.synchronize()
         p.sync_check(stream=s)
         assert torch.equal(u_graph, u_eager)
+
+
+def test_solve_host_pipelined_calls_match_device_solves(sem3d):
+    # Four back-to-back host-buffer solves (the two device buffer pairs rotate
+    # twice; copies of one call overlap the solve of the next) must equal the
+    # device-buffer solve of each input bit for bit.
+    n3, k, L3, c, (sx, sy, sz), _ = _case(3)
+    with sem3d.Plan(*n3, k, L3, c) as p:
+        p.set_precision("bf16x3", 3)
+        s = torch.cuda.Stream()
+        fs = [torch.from_numpy(random_rhs(*n3, seed=900 + q)).pin_memory() for q in range(4)]
+        us = [torch.full(fs[0].shape, float("nan"), dtype=torch.float64).pin_memory() for _ in range(4)]
+        for q in range(4):
+            p.solve_host(fs[q], us[q], stream=s)
+        p.solve_host_wait(stream=s)
+        s.synchronize()
+        p.sync_check(stream=s)
+        for q in range(4):
+            f = fs[q].cuda()
+            u = torch.empty_like(f)
+            p.solve(f, u)
+            p.sync_check()
+            assert torch.equal(us[q], u.cpu()), q
