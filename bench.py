@@ -42,8 +42,11 @@ def tc_traffic_per_launch(n: int):
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_inputs.json")) as fh:
             rec = json.load(fh)
-        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                h.update(fh.read())
+        sha = h.hexdigest()
     except (OSError, ValueError, KeyError):
         return None
     if not sha.startswith(rec["source_sha256_prefix"]):
@@ -306,6 +309,32 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "dmma_achieved_tflops": 2.0 * n**4 / (f64_ms / max(1, f64_n) / 1e3) / 1e12}
         plan.set_precision("bf16x3", args.sweeps)
 
+    # ---- TF32 tensor-core tier (the single-precision arithmetic of Table 10):
+    # bare (0 sweeps) and with FP64 refinement sweeps
+    tf32 = None
+    if args.tf32_steps > 0:
+        u_ex = torch.from_numpy(u_ex_h).cuda()
+        # TF32 dense peak: the measured sustained bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25 PF/s)
+        tf32_peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])) * 1.1 / 2.25
+        tf32 = {"path": "tcgen05 kind::tf32 mode products (rotating K-major layouts)", "steps": args.tf32_steps,
+                "warmup": 1, "tf32_peak_tflops": tf32_peak,
+                "tf32_peak_source": f"{peak_src} bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16 ratio)"}
+        for label, sw in (("bare", 0), ("refined", args.tf32_sweeps)):
+            plan.set_precision("tf32", sw)
+            plan.profile(True)
+            ms_t = timed(step, args.tf32_steps, 1, stream, torch, dist)
+            t_n, t_ms = plan.profile_read("tc_mode_product")
+            plan.profile(False)
+            plan.sync_check(stream)
+            tf32[label] = {"sweeps": sw, "ms_per_step": ms_t, "value": job_throughput(dofs, world, ms_t) / 1e9,
+                           "unit": "GDoF/s", "rel_linf_vs_exact_solution":
+                           float((u - u_ex).abs().max() / u_ex.abs().max()),
+                           "tc_avg_ms": t_ms / max(1, t_n),
+                           "tc_tflops": 2.0 * n**4 / (t_ms / max(1, t_n) / 1e3) / 1e12}
+            tf32[label]["tc_frac_of_tf32_peak"] = tf32[label]["tc_tflops"] / tf32_peak
+        del u_ex
+        plan.set_precision("bf16x3", args.sweeps)
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if args.e2e:
@@ -364,7 +393,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": t_setup},
         "accuracy": {"rel_linf_vs_exact_solution": err_exact, "rel_residual_linf": rel_res},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
-        "fp64_path": fp64, "bf16x3_fp64_residuals": f64res, "bf16x3_df_residuals": dfres, "e2e": e2e,
+        "fp64_path": fp64, "tf32_path": tf32, "bf16x3_fp64_residuals": f64res, "bf16x3_df_residuals": dfres, "e2e": e2e,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -478,6 +507,9 @@ def main():
     ap.add_argument("--fp64-residual-steps", type=int, default=3,
                     help="also time the BF16x3 path with FP64 residuals in every sweep (0 = skip)")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--tf32-steps", type=int, default=5,
+                    help="timed solves of the TF32 tier (bare, and refined with --tf32-sweeps); 0 skips it")
+    ap.add_argument("--tf32-sweeps", type=int, default=5)
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -55,6 +55,13 @@ typedef enum {
 /* Arithmetic of the six mode products of one solve (Section 2.4, Eq. 13).
  *   SEM3D_FP64   : FP64 operands and accumulation (mma.sync DMMA).
  *   SEM3D_FP32   : FP32 operands and accumulation on the CUDA cores (FFMA).
+ *   SEM3D_TF32   : operands rounded to TF32 (10-bit mantissa), one product
+ *                  per element pair, FP32 accumulation on tcgen05 tensor
+ *                  cores: the single-precision tensor-core arithmetic of
+ *                  Section 3.7 (Table 10).  Each pass contracts the fastest
+ *                  axis of its input and writes its output transposed, so
+ *                  all operands are K-major.  Not available to the
+ *                  Cahn-Hilliard step (SEM3D_ERR_UNSUPPORTED).
  *   SEM3D_BF16   : operands rounded to bfloat16, one product per element pair,
  *                  FP32 accumulation on tcgen05 tensor cores (~8 bits).
  *   SEM3D_BF16X3 : operands split x = hi + lo into two bfloat16 numbers;
@@ -68,6 +75,7 @@ typedef enum {
 typedef enum {
   SEM3D_FP64 = 0,
   SEM3D_FP32 = 1,
+  SEM3D_TF32 = 2,
   SEM3D_BF16 = 4,
   SEM3D_BF16X3 = 5,
   SEM3D_F16X3 = 6

@@ -33,3 +33,4 @@ from .sem import (  # noqa: F401
     assembled_h3,
     ch_step,
 )
+from .tf32 import tf32_round, tf32_operand, fast_solve_rounded  # noqa: F401

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsem3d.so")
-SOURCES = ["api.cu", "fp64_kernels.cu", "fp32_kernels.cu", "tc_kernels.cu", "pcg_kernels.cu", "ch_kernels.cu", "setup1d.cpp"]
+SOURCES = ["api.cu", "fp64_kernels.cu", "fp32_kernels.cu", "tc_kernels.cu", "tf32_kernels.cu", "pcg_kernels.cu", "ch_kernels.cu", "setup1d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,7 @@ def _newer(target: str, deps) -> bool:
 def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "sem3d.h"))
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "-I", os.path.join(ROOT, "include")]
     if ptxas_verbose:

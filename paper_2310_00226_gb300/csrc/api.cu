@@ -2,6 +2,7 @@
 // one solve (Section 2.4, Eq. 13) plus FP64 iterative refinement.
 #include "sem3d_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -175,13 +176,24 @@ struct LaunchScope {
 // Workspace layout per mode.
 //   FP64   : two FP64 n^3 arrays (ping-pong) + one FP64 residual array.
 //   FP32   : two FP32 n^3 arrays (ping-pong) + one FP64 residual array.
+//   TF32   : two FP32 arrays holding the largest of the rotated layouts
+//            (x, y, z)/(y, z, x)/(z, x, y), each at its padded pitch, + one
+//            FP64 residual array.
 //   BF16X3 / BF16 : three split arrays {hi, lo} of Px*ny*nz bf16 each (the
 //            third serves the Cahn-Hilliard step), and the double-FP32
 //            solution (two FP32 n^3 arrays) used between sweeps.
+// Elements of the largest rotated TF32 layout: pitch pad16 of the fastest axis.
+size_t tf32_elems(const Geom& g) {
+  const size_t a = (size_t)pad16(g.nx) * g.ny * g.nz, b = (size_t)pad16(g.ny) * g.nz * g.nx,
+               c = (size_t)pad16(g.nz) * g.nx * g.ny;
+  return std::max(a, std::max(b, c));
+}
+
 size_t workspace_bytes(const sem3d_plan* p) {
   const size_t N = (size_t)p->g.nx * p->g.ny * p->g.nz;
   if (p->prec == SEM3D_FP64) return 3 * align256(N * sizeof(double));
   if (p->prec == SEM3D_FP32) return 2 * align256(N * sizeof(float)) + align256(N * sizeof(double));
+  if (p->prec == SEM3D_TF32) return 2 * align256(tf32_elems(p->g) * sizeof(float)) + align256(N * sizeof(double));
   const size_t Ns = (size_t)p->g.Px * p->g.ny * p->g.nz;
   return 6 * align256(Ns * sizeof(__nv_bfloat16)) + 2 * align256(Ns * sizeof(float));
 }
@@ -233,6 +245,43 @@ sem3d_status solve_once_f32(sem3d_plan* p, const double* in, double* out, bool a
   LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 1, d[1].Wf[1], B, false, A, false, EPI_STORE, lx, ly, lz, s));
   LAUNCH(p, K_F32, 1, s, launch_mode_product_f32(g, 2, d[2].Wf[1], A, false, out, true,
                                                  accumulate ? EPI_ACCUM : EPI_STORE, lx, ly, lz, s));
+  return SEM3D_OK;
+}
+
+// ---- TF32 path (rotating layouts, see tf32_kernels.cu): FP64 in -> FP64 out
+// (store or accumulate).  Passes x, y, z (forward, division fused into the z
+// pass) then x, y, z (backward); the arrays alternate between A and B.
+sem3d_status solve_once_tf32(sem3d_plan* p, const double* in, double* out, bool accumulate, cudaStream_t s) {
+  const Geom& g = p->g;
+  float* A = static_cast<float*>(p->ws);
+  float* B = reinterpret_cast<float*>(static_cast<char*>(p->ws) + align256(tf32_elems(g) * sizeof(float)));
+  const DevAxis* d = p->dev;
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const int P3[3] = {pad16(g.nx), pad16(g.ny), pad16(g.nz)};
+  LAUNCH(p, K_SPLIT, 1, s, launch_to_tf32(g, in, A, s));
+  float* bufs[2] = {A, B};
+  for (int q = 0; q < 6; ++q) {
+    const int ax = q % 3, a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;  // contracted axis, then the two row axes
+    Tf32Pass t;
+    t.nK = n3[ax]; t.d1 = n3[a1]; t.d2 = n3[a2]; t.P0 = P3[ax];
+    t.in = bufs[q & 1];
+    t.W = d[ax].Wt32[q < 3 ? 0 : 1];
+    t.Wpitch = d[ax].Kp;
+    if (q < 5) {
+      t.out32 = bufs[(q + 1) & 1];
+      t.P1 = P3[a1];
+      t.epi = q == 2 ? EPI_DIV : EPI_STORE;
+      // pass 3 rows (a, b), output c: lam_x[a] + lam_y[b] + lam_z[c]
+      t.lam1 = d[0].lamf; t.lam2 = d[1].lamf; t.lam3 = d[2].lamf;
+      t.c = (float)g.c;
+    } else {
+      t.out64 = out;
+      t.P1 = g.nx;  // dense FP64 solution, x fastest
+      t.epi = accumulate ? EPI_ACCUM : EPI_STORE;
+    }
+    const int sub = ax == 0 ? K_TC_X : ax == 1 ? K_TC_Y : K_TC_Z;
+    LAUNCH_SUB(p, K_TC, q == 5 ? K_TC_F64OUT : sub, 1, s, launch_mode_product_tf32(t, p->d_err, p->num_sms, s));
+  }
   return SEM3D_OK;
 }
 
@@ -348,6 +397,13 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
       std::vector<float> wf(Wd.begin(), Wd.end());
       if ((st = dev_upload(p.get(), &D.Wf[w], wf.data(), wf.size())) != SEM3D_OK) return st;
     }
+    for (int w = 0; w < 2; ++w) {  // TF32-rounded W for the TF32 tier, row pitch Kp
+      const std::vector<double>& Wd = (w == 0) ? A.Tinv : A.T;
+      std::vector<float> wt((size_t)A.n * D.Kp, 0.f);
+      for (int o = 0; o < A.n; ++o)
+        for (int t = 0; t < A.n; ++t) wt[(size_t)o * D.Kp + t] = tf32_round((float)Wd[(size_t)o * A.n + t]);
+      if ((st = dev_upload(p.get(), &D.Wt32[w], wt.data(), wt.size())) != SEM3D_OK) return st;
+    }
     for (int w = 0; w < 2; ++w) {  // fp16 pairs of W * 2^eW for the F16X3 tier
       const std::vector<double>& Wd = (w == 0) ? A.Tinv : A.T;
       const int n = A.n;
@@ -397,12 +453,13 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
 
 sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweeps) {
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
-  if (prec != SEM3D_FP64 && prec != SEM3D_FP32 && prec != SEM3D_BF16 && prec != SEM3D_BF16X3 && prec != SEM3D_F16X3)
+  if (prec != SEM3D_FP64 && prec != SEM3D_FP32 && prec != SEM3D_TF32 && prec != SEM3D_BF16 && prec != SEM3D_BF16X3 &&
+      prec != SEM3D_F16X3)
     return fail(SEM3D_ERR_INVALID_ARG, "unknown precision");
   if (prec == SEM3D_F16X3 && (h->k > 8 || h->g.bc != 0))
     return fail(SEM3D_ERR_UNSUPPORTED, "F16X3 needs k <= 8 and Dirichlet data");
   if (sweeps < 0 || sweeps > 16) return fail(SEM3D_ERR_INVALID_ARG, "sweeps must be in [0, 16]");
-  if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16 || prec == SEM3D_F16X3) {
+  if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16 || prec == SEM3D_F16X3 || prec == SEM3D_TF32) {
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
@@ -539,6 +596,13 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
     for (int sw = 0; sw < h->sweeps; ++sw) {
       LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
       if ((st = solve_once_f32(h, r, u, true, s)) != SEM3D_OK) return st;
+    }
+  } else if (h->prec == SEM3D_TF32) {
+    double* r = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(tf32_elems(h->g) * sizeof(float)));
+    if ((st = solve_once_tf32(h, f, u, false, s)) != SEM3D_OK) return st;
+    for (int sw = 0; sw < h->sweeps; ++sw) {
+      LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+      if ((st = solve_once_tf32(h, r, u, true, s)) != SEM3D_OK) return st;
     }
   } else {
     const size_t Ns = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(__nv_bfloat16));
@@ -888,6 +952,7 @@ sem3d_status ch_step_core(sem3d_plan* h, const double* phi_n, const double* phi_
 sem3d_status ch_check(sem3d_plan* h, double eps, double m, double dt, double S) {
   if (!(eps > 0.0) || !(m > 0.0) || !(dt > 0.0) || !(S >= 0.0) || !std::isfinite(eps + m + dt + S))
     return fail(SEM3D_ERR_INVALID_ARG, "need eps, m, dt > 0 and S >= 0");
+  if (h->prec == SEM3D_TF32) return fail(SEM3D_ERR_UNSUPPORTED, "the Cahn-Hilliard step has no TF32 tier");
   return ensure_workspace(h);
 }
 

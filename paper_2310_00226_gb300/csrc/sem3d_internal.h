@@ -7,6 +7,7 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -42,6 +43,22 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const unsigned int q = (unsigned int)(sig >> sh);
   const unsigned long long rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
   return __uint_as_float(sign | (q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u)));
+}
+
+// Round an FP32 value to TF32 (10 explicit mantissa bits) to nearest, ties to
+// even, on the binary32 bit pattern; the result is an FP32 number whose 13 low
+// mantissa bits are zero.  Infinities and NaN pass through; finite values
+// that round past the largest TF32 number become infinity.
+__host__ __device__ inline float tf32_round(float x) {
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  if ((b & 0x7F800000u) != 0x7F800000u) {
+    b += 0xFFFu + ((b >> 13) & 1u);
+    b &= 0xFFFFE000u;
+  }
+  float y;
+  memcpy(&y, &b, 4);
+  return y;
 }
 #endif
 
@@ -95,6 +112,7 @@ struct DevAxis {
   int* band_lo = nullptr;
   int* band_hi = nullptr;
   float* Wf[2] = {nullptr, nullptr};            // FP32 copies: [0] = T^{-1}, [1] = T; n x n row-major
+  float* Wt32[2] = {nullptr, nullptr};          // TF32-rounded copies, n rows x Kp (TF32 tier)
   __nv_bfloat16* W_hi[2] = {nullptr, nullptr};  // [0] = T^{-1}, [1] = T; n rows x Kp
   // F16X3 tier: W * 2^eW16 split into fp16 hi + lo (same layout), and the
   // infinity norm of W (largest row sum of |W|) for the scale bounds.
@@ -209,6 +227,31 @@ struct TcPassPlan;
 // Failure-detection testing: the next `launches` tensor-core launches of the
 // process issue no operand loads, so their bounded waits expire.
 void tc_inject_stall(int launches);
+// Takes one launch from the pending sem3d_inject_stall count: 1 if this
+// launch must run with its producer stalled, else 0.
+int tc_take_stall();
+
+// One TF32 mode product of the rotating-layout solve (tf32_kernels.cu): the
+// input has dims (nK, d1, d2), nK fastest at row pitch P0 (a multiple of 4);
+// W is nK x nK, row o at W + o*Wpitch (TF32-rounded FP32).  The output element
+// (i1, i2, o) goes to i1 + P1*(i2 + d2*o) of out32 (TF32-rounded; epi
+// EPI_STORE or EPI_DIV with lam1[i1] + lam2[i2] + lam3[o] + c) or of out64
+// (EPI_STORE or EPI_ACCUM).
+struct Tf32Pass {
+  int nK = 0, d1 = 0, d2 = 0, P0 = 0;
+  const float* in = nullptr;
+  const float* W = nullptr;
+  int Wpitch = 0;
+  float* out32 = nullptr;
+  double* out64 = nullptr;
+  long long P1 = 0;
+  int epi = EPI_STORE;
+  const float *lam1 = nullptr, *lam2 = nullptr, *lam3 = nullptr;
+  float c = 0.f;
+};
+cudaError_t launch_mode_product_tf32(const Tf32Pass& p, int* err_flag, int num_sms, cudaStream_t s);
+// FP64 x-fastest array (pitch nx) -> TF32-rounded FP32 at pitch g.Px.
+cudaError_t launch_to_tf32(const Geom& g, const double* in, float* out, cudaStream_t s);
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,

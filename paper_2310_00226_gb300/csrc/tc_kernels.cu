@@ -29,11 +29,9 @@
 // records SEM3D_ERR_TIMEOUT in *err, drains its own copies and MMAs, frees
 // TMEM and returns.
 #include "sem3d_internal.h"
-
-#include <cudaTypedefs.h>
+#include "tc_ptx.cuh"
 
 #include <atomic>
-#include <mutex>
 
 namespace sem3d {
 
@@ -60,111 +58,6 @@ constexpr int TMEM_COLS = 2 * BN;  // 512
 // with the MMAs.  Threads: producer warp, MMA warp, epilogue warps.
 __host__ __device__ constexpr int epi_warps(int mode) { return mode >= 2 ? 16 : 8; }
 __host__ __device__ constexpr int num_threads(int mode) { return 64 + 32 * epi_warps(mode); }
-constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s per wait
-
-// ---------------------------------------------------------------- PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase.  Returns false when the wait expires
-// (recording SEM3D_ERR_TIMEOUT in *err) or, while err is non-null, when
-// another thread of the grid has already recorded an error.  err == nullptr
-// is used by the final drains: they only bound the wait.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0) {
-      if (err != nullptr && *reinterpret_cast<volatile int*>(err) != 0) return false;
-      if (globaltimer() - t0 > WAIT_NS) {
-        if (err != nullptr) atomicOr(err, 1 << SEM3D_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
-                                            int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (>>4), fixed version 1 at bit 46, swizzle layout code
-// at bits 61-63 (2 = 128-byte swizzle, 4 = 64-byte swizzle).
-constexpr uint32_t LAYOUT_SW128 = 2, LAYOUT_SW64 = 4;
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)layout << 61;
-  return d;
-}
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
 // B format at bits 7-9 and 10-12 (0 = fp16, 1 = bf16; both operands of one
@@ -183,52 +76,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Arrive on the mbarrier at the same offset in every CTA of `mask` once all
-// tcgen05 operations issued so far by this thread have completed.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-               ::"r"(bar), "h"(mask)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
-      "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
-      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
-      "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
-      "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
-      "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- kernel
 
@@ -295,18 +142,6 @@ __device__ __forceinline__ int f16_exponent(float bound) {
 }
 
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
-
-// Exact FP32 -> FP64 conversion with integer operations (keeps the FP64 pipe,
-// ~1/64 of the FP32 rate on this GPU, free for the update's addition).
-// FP32 subnormals (|x| < 1.2e-38) become signed zero; Inf/NaN are kept.
-__device__ __forceinline__ double f32_to_f64(float x) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t e = (b >> 23) & 0xFFu;
-  const uint64_t sign = (uint64_t)(b >> 31) << 63;
-  const uint64_t e64 = (e == 0xFFu) ? 0x7FFull : (uint64_t)(e + 896u);
-  const uint64_t bits = sign | (e64 << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)(e == 0u ? sign : bits));
-}
 
 __device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
   asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"((unsigned short)(v & 0xFFFFu)) : "memory");
@@ -784,36 +619,6 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
   }
 }
 
-// ---------------------------------------------------------------- host side
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
-bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
-              const uint32_t* box, CUtensorMapSwizzle swz) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t gd[3], gs[2];
-  cuuint32_t bx[3], es[3] = {1, 1, 1};
-  for (int r = 0; r < rank; ++r) { gd[r] = dims[r]; bx[r] = box[r]; }
-  for (int r = 0; r + 1 < rank; ++r) gs[r] = strides_bytes[r];
-  CUresult res = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return res == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 namespace {
@@ -929,6 +734,13 @@ std::atomic<int> g_stall_launches{0};
 
 void tc_inject_stall(int launches) { g_stall_launches.store(launches); }
 
+int tc_take_stall() {
+  int left = g_stall_launches.load();
+  while (left > 0 && !g_stall_launches.compare_exchange_weak(left, left - 1)) {
+  }
+  return left > 0 ? 1 : 0;
+}
+
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
                                        TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
                                        const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
@@ -947,12 +759,7 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   }
   if (out64 && epi == EPI_DIV) return cudaErrorInvalidValue;
   TcArgs a{};
-  {
-    int left = g_stall_launches.load();
-    while (left > 0 && !g_stall_launches.compare_exchange_weak(left, left - 1)) {
-    }
-    a.stall = left > 0 ? 1 : 0;
-  }
+  a.stall = tc_take_stall();
   a.df_hi = df.hi;
   a.df_lo = df.lo;
   if (f16) {

@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsem3d.s
 
 SEM3D_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "UNSUPPORTED"}
-PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 4, "bf16x3": 5, "f16x3": 6}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 4, "bf16x3": 5, "f16x3": 6}
 
 #: Every entry point declared in include/sem3d.h.
 EXPORTS = (

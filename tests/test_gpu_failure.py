@@ -29,8 +29,8 @@ def sem3d():
     return mod
 
 
-@pytest.mark.parametrize("tier", ["bf16x3", "f16x3"])
-def test_expired_wait_is_reported_and_the_plan_recovers(sem3d, tier):
+@pytest.mark.parametrize("tier,sweeps", [("bf16x3", 3), ("f16x3", 3), ("tf32", 5)])
+def test_expired_wait_is_reported_and_the_plan_recovers(sem3d, tier, sweeps):
     n3, k = (63, 31, 47), 2
     axes = [sem_1d(k, (n + 1) // k, 0.0, 1.0) for n in n3]
     F = random_rhs(*n3, seed=17)
@@ -47,7 +47,7 @@ def test_expired_wait_is_reported_and_the_plan_recovers(sem3d, tier):
             p.sync_check()
         assert exc.value.status == TIMEOUT
         # the error word was cleared and the context is usable: a normal refined solve
-        p.set_precision(tier, 3)
+        p.set_precision(tier, sweeps)
         p.solve(f, u)
         p.sync_check()
         err = float(np.abs(u.cpu().numpy() - ref).max() / np.abs(ref).max())

@@ -267,7 +267,7 @@ def test_solve_is_repeatable_and_stream_ordered(sem3d):
         assert torch.equal(u1, u2)
 
 
-@pytest.mark.parametrize("tier,sweeps", [("bf16x3", 3), ("f16x3", 3), ("fp32", 2), ("fp64", 1)])
+@pytest.mark.parametrize("tier,sweeps", [("bf16x3", 3), ("f16x3", 3), ("fp32", 2), ("fp64", 1), ("tf32", 4)])
 def test_solve_captures_into_a_cuda_graph(sem3d, tier, sweeps):
     # With a fixed sweep count the solve makes no host synchronisation, so it can
     # be captured in a CUDA graph; replays must equal the eager result bit for bit.
