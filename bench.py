@@ -509,7 +509,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--tf32-steps", type=int, default=5,
                     help="timed solves of the TF32 tier (bare, and refined with --tf32-sweeps); 0 skips it")
-    ap.add_argument("--tf32-sweeps", type=int, default=5)
+    ap.add_argument("--tf32-sweeps", type=int, default=7)
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

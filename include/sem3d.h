@@ -116,7 +116,13 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
  * iterative-refinement sweeps (each sweep: FP64 residual r = f - (c + H_x (+)
  * H_y (+) H_z) u with the banded operator of Eq. 12, a solve of the correction
  * in the selected arithmetic, u += correction).  sweeps in [0, 16].
- * With a fixed sweep count the solve performs no host synchronisation. */
+ * With a fixed sweep count the solve performs no host synchronisation.
+ * Errors: SEM3D_ERR_INVALID_ARG for an unknown precision or sweep count;
+ * SEM3D_ERR_UNSUPPORTED for the tensor-core tiers (TF32, BF16, BF16X3,
+ * F16X3) on a GPU other than sm_103, and for F16X3 with k > 8 or Neumann
+ * data.  A plan-owned workspace grows on the next solve if the new tier
+ * needs more (sem3d_workspace_size); with a caller-owned workspace that is
+ * too small the next solve fails with SEM3D_ERR_INVALID_ARG. */
 sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
 
 /* Arithmetic of the refinement residuals in the SEM3D_BF16X3 / F16X3 tiers.

@@ -256,18 +256,24 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
 }
 
 // FP64 array (x fastest, pitch nx) -> TF32-rounded FP32 array at pitch Px.
-// One warp per x-line segment of 32; lines are walked by the whole grid.
+// Blocks walk the (j, l) lines; a lane converts 4 consecutive entries and
+// writes them as one 16-byte store (rows of pitch Px, a multiple of 16, are
+// 64-byte aligned); the pad entries i >= nx are written as zeros.
 __global__ void __launch_bounds__(256) to_tf32_kernel(const double* __restrict__ in, float* __restrict__ out, int nx,
                                                       int Px, long long lines) {
-  const int segs = (nx + 31) >> 5;
-  const long long total = lines * segs;
-  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  for (long long w = warp0; w < total; w += nwarps) {
-    const long long line = w / segs;
-    const int i = (int)(w - line * segs) * 32 + lane;
-    if (i < nx) out[line * Px + i] = tf32_round(f64_to_f32_rn(in[line * nx + i]));
+  const int chunks = Px >> 2;
+  for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
+    const double* row = in + line * nx;
+    float4* orow = reinterpret_cast<float4*>(out + line * Px);
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+      const int i = 4 * c;
+      float4 v;
+      v.x = i < nx ? tf32_round(f64_to_f32_rn(row[i])) : 0.f;
+      v.y = i + 1 < nx ? tf32_round(f64_to_f32_rn(row[i + 1])) : 0.f;
+      v.z = i + 2 < nx ? tf32_round(f64_to_f32_rn(row[i + 2])) : 0.f;
+      v.w = i + 3 < nx ? tf32_round(f64_to_f32_rn(row[i + 3])) : 0.f;
+      orow[c] = v;
+    }
   }
 }
 
@@ -306,10 +312,8 @@ cudaError_t launch_tf32(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32
 
 cudaError_t launch_to_tf32(const Geom& g, const double* in, float* out, cudaStream_t s) {
   const long long lines = (long long)g.ny * g.nz;
-  const long long warps = lines * ((g.nx + 31) / 32);
-  long long blocks = (warps + 7) / 8;
-  if (blocks > 152LL * 16) blocks = 152LL * 16;
-  to_tf32_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(in, out, g.nx, g.Px, lines);
+  const long long blocks = lines < 152LL * 16 ? (lines < 1 ? 1 : lines) : 152LL * 16;
+  to_tf32_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, g.nx, g.Px, lines);
   return cudaGetLastError();
 }
 
