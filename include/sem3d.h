@@ -137,12 +137,15 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
  *                          (FP64) residual.  Applies for k <= 8 and s >= 2;
  *                          otherwise every sweep is FP64.
  *   SEM3D_RESIDUAL_DF    : every sweep in double-FP32 arithmetic, the last one
- *                          writing the FP64 solution.  Not FP64 refinement:
- *                          the residual carries ~2^-48 of the operator's terms,
- *                          amplified by the conditioning of the operator:
- *                          measured forward error 2e-12 at n=383, 8e-11 at
- *                          n=999 (against 6e-15 with the FP64 last sweep),
- *                          in 14% less time; for k <= 8 with Dirichlet data,
+ *                          writing the FP64 solution; the rows of H enter as
+ *                          exact three-term FP32 sums (a 48-bit operator
+ *                          would be a different operator: 8e-11 at n=999).
+ *                          Not FP64 refinement: the residual carries ~2^-48
+ *                          of the operator's terms, amplified by the
+ *                          conditioning of the operator: measured 1.5e-12 at
+ *                          n=383 and 7e-12 at n=999 from the FP64-residual
+ *                          result (against 9e-15 with the FP64 last sweep),
+ *                          in 11% less time; for k <= 8 with Dirichlet data,
  *                          else every sweep is FP64.
  * The FP64 tier always uses FP64 residuals. */
 typedef enum { SEM3D_RESIDUAL_FP64 = 0, SEM3D_RESIDUAL_MIXED = 1, SEM3D_RESIDUAL_DF = 2 } sem3d_residual;

@@ -380,15 +380,23 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
       if (a == 0)
         for (int q = 0; q < k; ++q) hq[(size_t)q * (2 * k + 1) + k] += c;
       if ((st = dev_upload(p.get(), &D.Hq, hq.data(), hq.size())) != SEM3D_OK) return st;
-      std::vector<float> hh(hq.size()), hl(hq.size());
+      // Three FP32 terms: hi + lo holds 48 bits; the remainder lo2 makes the
+      // sum exact (53 bits need at most three 24-bit pieces).
+      std::vector<float> hh(hq.size()), hl(hq.size()), hl2(hq.size());
       for (size_t q = 0; q < hq.size(); ++q) {
         hh[q] = (float)hq[q];
         hl[q] = (float)(hq[q] - (double)hh[q]);
+        hl2[q] = (float)(hq[q] - (double)hh[q] - (double)hl[q]);
       }
       if (k <= 4)
-        for (size_t q = 0; q < hq.size(); ++q) { D.Hq_hi_host[q] = hh[q]; D.Hq_lo_host[q] = hl[q]; }
+        for (size_t q = 0; q < hq.size(); ++q) {
+          D.Hq_hi_host[q] = hh[q];
+          D.Hq_lo_host[q] = hl[q];
+          D.Hq_lo2_host[q] = hl2[q];
+        }
       if ((st = dev_upload(p.get(), &D.Hq_hi, hh.data(), hh.size())) != SEM3D_OK) return st;
       if ((st = dev_upload(p.get(), &D.Hq_lo, hl.data(), hl.size())) != SEM3D_OK) return st;
+      if ((st = dev_upload(p.get(), &D.Hq_lo2, hl2.data(), hl2.size())) != SEM3D_OK) return st;
     }
     if ((st = dev_upload(p.get(), &D.band_lo, A.band_lo.data(), A.band_lo.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.band_hi, A.band_hi.data(), A.band_hi.size())) != SEM3D_OK) return st;
@@ -621,6 +629,10 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
                            : (h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2) ? sw - 1
                            : (h->residual == SEM3D_RESIDUAL_DF) ? sw : 0;
     const bool mixed = ndf > 0;
+    // Every residual in double-FP32: the operator's rows must then be exact
+    // (three FP32 terms), or the sweeps converge to the 48-bit operator's
+    // solution.  With a final FP64 sweep the 48-bit rows suffice.
+    const bool exact_coef = h->residual == SEM3D_RESIDUAL_DF;
     const bool f16 = h->prec == SEM3D_F16X3;
     // F16X3: the residual is written as FP32 into S1's storage (4 bytes per
     // entry at pitch Px fit in its hi + lo arrays) and then split with a
@@ -646,13 +658,15 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
       for (int q = 1; q <= ndf; ++q) {
         if (f16) {
           if ((st = reset_scales()) != SEM3D_OK) return st;
-          LAUNCH(h, K_STENCIL, 1, s, launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16));
+          LAUNCH(h, K_STENCIL, 1, s,
+                 launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16, exact_coef));
           LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
         } else {
           // k in {1, 2, 4}: one vector kernel that also writes the pads; otherwise
           // the element kernel plus a pad-zeroing kernel when Px > nx
           const int df_launches = (h->k == 1 || h->k == 2 || h->k == 4 || h->g.Px == h->g.nx) ? 1 : 2;
-          LAUNCH(h, K_STENCIL, df_launches, s, launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s));
+          LAUNCH(h, K_STENCIL, df_launches, s,
+                 launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s, nullptr, nullptr, exact_coef));
         }
         const bool last_df = (q == ndf);
         if ((st = solve_once_bf16x3(h, S0, S1, last_df ? u : nullptr, last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, D,

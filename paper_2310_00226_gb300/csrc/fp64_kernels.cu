@@ -355,11 +355,14 @@ __device__ __forceinline__ void f64_to_df(double x, float& hi, float& lo) {
   lo = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) | sign);
 }
 
-// (ah, al) -= (ch + cl) * (uh + ul), dropping cl*ul.
-__device__ __forceinline__ void df_sub_prod(float& ah, float& al, float ch, float cl, float uh, float ul) {
+// (ah, al) -= (ch + cl [+ cl2]) * (uh + ul), dropping cl*ul and cl2*ul; the
+// third coefficient term cl2 enters only when EXACT (else the 48-bit ch + cl).
+template <bool EXACT = false>
+__device__ __forceinline__ void df_sub_prod(float& ah, float& al, float ch, float cl, float uh, float ul,
+                                            float cl2 = 0.f) {
   const float p = ch * uh;
   const float e = fmaf(ch, uh, -p);
-  const float t = fmaf(ch, ul, fmaf(cl, uh, e));
+  const float t = fmaf(ch, ul, fmaf(cl, uh, EXACT ? fmaf(cl2, uh, e) : e));
   const float s = ah - p;
   const float bb = s - ah;
   const float err = (ah - (s - bb)) - (p + bb);
@@ -376,10 +379,11 @@ struct DfArgs {
   float* out32;        // if set: FP32 residual at pitch Px, max |r| -> st slot 0
   F16State* st;
   const float *Hxh, *Hxl, *Hyh, *Hyl, *Hzh, *Hzl;
+  const float *Hxl2, *Hyl2, *Hzl2;  // third coefficient terms (read when EXACT)
   int nx, ny, nz, Px, nex;
 };
 
-template <int K>
+template <int K, bool EXACT>
 __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
   constexpr int BW = 2 * K + 1;
   const long long lines = (long long)a.ny * a.nz;
@@ -413,8 +417,8 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
       const int dlo = (q == 0) ? -K : -q, dhi = (q == 0) ? K : K - q;
 #pragma unroll
       for (int d = dlo; d <= dhi; ++d)
-        df_sub_prod(ah[q], al[q], __ldg(a.Hxh + q * BW + d + K), __ldg(a.Hxl + q * BW + d + K), wh[K + q + d],
-                    wl[K + q + d]);
+        df_sub_prod<EXACT>(ah[q], al[q], __ldg(a.Hxh + q * BW + d + K), __ldg(a.Hxl + q * BW + d + K), wh[K + q + d],
+                    wl[K + q + d], EXACT ? __ldg(a.Hxl2 + q * BW + d + K) : 0.f);
     }
     {
       const int qy = (j + 1) % K;
@@ -423,12 +427,13 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
         const int jj = j + d;
         if (jj < 0 || jj >= a.ny) continue;
         const float ch = __ldg(a.Hyh + qy * BW + d + K), cl = __ldg(a.Hyl + qy * BW + d + K);
+        const float cl2 = EXACT ? __ldg(a.Hyl2 + qy * BW + d + K) : 0.f;
         const long long off = ((long long)l * a.ny + jj) * a.Px;
 #pragma unroll
         for (int q = 0; q < K; ++q) {
           const int i = i0 + q;
           if (i < 0) continue;
-          df_sub_prod(ah[q], al[q], ch, cl, __ldg(a.uh + off + i), __ldg(a.ul + off + i));
+          df_sub_prod<EXACT>(ah[q], al[q], ch, cl, __ldg(a.uh + off + i), __ldg(a.ul + off + i), cl2);
         }
       }
     }
@@ -439,12 +444,13 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
         const int ll = l + d;
         if (ll < 0 || ll >= a.nz) continue;
         const float ch = __ldg(a.Hzh + qz * BW + d + K), cl = __ldg(a.Hzl + qz * BW + d + K);
+        const float cl2 = EXACT ? __ldg(a.Hzl2 + qz * BW + d + K) : 0.f;
         const long long off = ((long long)ll * a.ny + j) * a.Px;
 #pragma unroll
         for (int q = 0; q < K; ++q) {
           const int i = i0 + q;
           if (i < 0) continue;
-          df_sub_prod(ah[q], al[q], ch, cl, __ldg(a.uh + off + i), __ldg(a.ul + off + i));
+          df_sub_prod<EXACT>(ah[q], al[q], ch, cl, __ldg(a.uh + off + i), __ldg(a.ul + off + i), cl2);
         }
       }
     }
@@ -483,6 +489,7 @@ __global__ void __launch_bounds__(256) stencil_df_kernel(DfArgs a) {
 struct DfCoef {
   float h[3][4 * 9];
   float l[3][4 * 9];
+  float l2[3][4 * 9];  // third terms (used when EXACT)
 };
 
 // Double-FP32 residual for k in {1, 2, 4}.  A lane handles the 4 consecutive
@@ -492,7 +499,7 @@ struct DfCoef {
 // the line's Px/4 chunks.  Since 4 % k == 0, node 4c+p has the local index
 // (p+1) % k for every c: each position's x row of H is known at compile time
 // and only its band is summed.  The y and z rows depend on the warp's (j, l).
-template <int K>
+template <int K, bool EXACT>
 __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __grid_constant__ DfCoef cf) {
   constexpr int BW = 2 * K + 1;
   const int lane = threadIdx.x & 31;
@@ -538,29 +545,32 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
 #pragma unroll
         for (int d = -K; d <= K; ++d)
           if (d >= dlo && d <= dhi)  // compile-time after unrolling
-            df_sub_prod(ah[p], al[p], cf.h[0][q * BW + d + K], cf.l[0][q * BW + d + K], wh[4 + p + d], wl[4 + p + d]);
+            df_sub_prod<EXACT>(ah[p], al[p], cf.h[0][q * BW + d + K], cf.l[0][q * BW + d + K], wh[4 + p + d], wl[4 + p + d],
+                        EXACT ? cf.l2[0][q * BW + d + K] : 0.f);
       }
       // y and z: the rows of the neighbouring lines, one float4 pair per row
 #pragma unroll
       for (int d = -K; d <= K; ++d) {
         if (d < ylo || d > yhi || j + d < 0 || j + d >= a.ny) continue;  // warp-uniform
         const float chh = cf.h[1][qy * BW + d + K], cll = cf.l[1][qy * BW + d + K];
+        const float cl2 = EXACT ? cf.l2[1][qy * BW + d + K] : 0.f;
         const float4 vh = __ldg(UH + row4 + (long long)d * chunks + c), vl = __ldg(UL + row4 + (long long)d * chunks + c);
-        df_sub_prod(ah[0], al[0], chh, cll, vh.x, vl.x);
-        df_sub_prod(ah[1], al[1], chh, cll, vh.y, vl.y);
-        df_sub_prod(ah[2], al[2], chh, cll, vh.z, vl.z);
-        df_sub_prod(ah[3], al[3], chh, cll, vh.w, vl.w);
+        df_sub_prod<EXACT>(ah[0], al[0], chh, cll, vh.x, vl.x, cl2);
+        df_sub_prod<EXACT>(ah[1], al[1], chh, cll, vh.y, vl.y, cl2);
+        df_sub_prod<EXACT>(ah[2], al[2], chh, cll, vh.z, vl.z, cl2);
+        df_sub_prod<EXACT>(ah[3], al[3], chh, cll, vh.w, vl.w, cl2);
       }
 #pragma unroll
       for (int d = -K; d <= K; ++d) {
         if (d < zlo || d > zhi || l + d < 0 || l + d >= a.nz) continue;  // warp-uniform
         const float chh = cf.h[2][qz * BW + d + K], cll = cf.l[2][qz * BW + d + K];
+        const float cl2 = EXACT ? cf.l2[2][qz * BW + d + K] : 0.f;
         const float4 vh = __ldg(UH + row4 + (long long)d * splane + c);
         const float4 vl = __ldg(UL + row4 + (long long)d * splane + c);
-        df_sub_prod(ah[0], al[0], chh, cll, vh.x, vl.x);
-        df_sub_prod(ah[1], al[1], chh, cll, vh.y, vl.y);
-        df_sub_prod(ah[2], al[2], chh, cll, vh.z, vl.z);
-        df_sub_prod(ah[3], al[3], chh, cll, vh.w, vl.w);
+        df_sub_prod<EXACT>(ah[0], al[0], chh, cll, vh.x, vl.x, cl2);
+        df_sub_prod<EXACT>(ah[1], al[1], chh, cll, vh.y, vl.y, cl2);
+        df_sub_prod<EXACT>(ah[2], al[2], chh, cll, vh.z, vl.z, cl2);
+        df_sub_prod<EXACT>(ah[3], al[3], chh, cll, vh.w, vl.w, cl2);
       }
       float r[4];
 #pragma unroll
@@ -592,26 +602,32 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
 }
 
 template <int K>
-cudaError_t launch_df4(const DfArgs& a, const DevAxis* ax, cudaStream_t s) {
+cudaError_t launch_df4(const DfArgs& a, const DevAxis* ax, bool exact, cudaStream_t s) {
   DfCoef cf{};
   for (int w = 0; w < 3; ++w)
-    for (int e = 0; e < K * (2 * K + 1); ++e) { cf.h[w][e] = ax[w].Hq_hi_host[e]; cf.l[w][e] = ax[w].Hq_lo_host[e]; }
+    for (int e = 0; e < K * (2 * K + 1); ++e) {
+      cf.h[w][e] = ax[w].Hq_hi_host[e];
+      cf.l[w][e] = ax[w].Hq_lo_host[e];
+      cf.l2[w][e] = ax[w].Hq_lo2_host[e];
+    }
   // One block per 8 consecutive lines and no grid stride: the resident blocks
   // then sweep the grid plane by plane, so the rows 1..K planes away that a
   // warp reads were read moments earlier by other warps and are still in L2.
   const long long lines = (long long)a.ny * a.nz;
   long long blocks = (lines + 7) / 8;
   if (blocks > 0x7FFFFFFFLL) blocks = 0x7FFFFFFFLL;
-  stencil_df4_kernel<K><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a, cf);
+  if (exact) stencil_df4_kernel<K, true><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a, cf);
+  else stencil_df4_kernel<K, false><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a, cf);
   return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t launch_df(const DfArgs& a, cudaStream_t s) {
+cudaError_t launch_df(const DfArgs& a, bool exact, cudaStream_t s) {
   const long long total = (long long)a.nex * a.ny * a.nz;
   long long b = (total + 255) / 256;
   if (b > 0x7FFFFFFFLL) b = 0x7FFFFFFFLL;  // one thread per work item (see launch_elem)
-  stencil_df_kernel<K><<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+  if (exact) stencil_df_kernel<K, true><<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+  else stencil_df_kernel<K, false><<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -730,7 +746,7 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
                               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s, float* out32,
-                              F16State* st) {
+                              F16State* st, bool exact_coef) {
   if (g.bc != 0) return cudaErrorInvalidValue;  // element-pattern rows (Dirichlet) only
   DfArgs a{};
   a.uh = u.hi; a.ul = u.lo; a.f = f; a.hi = out_hi; a.lo = out_lo;
@@ -738,18 +754,19 @@ cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers
   a.Hxh = ax[0].Hq_hi; a.Hxl = ax[0].Hq_lo;
   a.Hyh = ax[1].Hq_hi; a.Hyl = ax[1].Hq_lo;
   a.Hzh = ax[2].Hq_hi; a.Hzl = ax[2].Hq_lo;
+  if (exact_coef) { a.Hxl2 = ax[0].Hq_lo2; a.Hyl2 = ax[1].Hq_lo2; a.Hzl2 = ax[2].Hq_lo2; }
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
   a.nex = (g.nx + 1) / k;
   cudaError_t e;
   switch (k) {
-    case 1: return launch_df4<1>(a, ax, s);  // pads written as zeros
-    case 2: return launch_df4<2>(a, ax, s);
-    case 4: return launch_df4<4>(a, ax, s);
-    case 3: e = launch_df<3>(a, s); break;
-    case 5: e = launch_df<5>(a, s); break;
-    case 6: e = launch_df<6>(a, s); break;
-    case 7: e = launch_df<7>(a, s); break;
-    case 8: e = launch_df<8>(a, s); break;
+    case 1: return launch_df4<1>(a, ax, exact_coef, s);  // pads written as zeros
+    case 2: return launch_df4<2>(a, ax, exact_coef, s);
+    case 4: return launch_df4<4>(a, ax, exact_coef, s);
+    case 3: e = launch_df<3>(a, exact_coef, s); break;
+    case 5: e = launch_df<5>(a, exact_coef, s); break;
+    case 6: e = launch_df<6>(a, exact_coef, s); break;
+    case 7: e = launch_df<7>(a, exact_coef, s); break;
+    case 8: e = launch_df<8>(a, exact_coef, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess || g.Px == g.nx || out32) return e;

@@ -105,10 +105,12 @@ struct DevAxis {
   float* lamf = nullptr;        // FP32 copy for the low-precision epilogues
   double* Hband = nullptr;      // FP64 n x (2k+1)
   double* Hq = nullptr;         // FP64 k x (2k+1) per-local-index rows of H (x axis: + c on the diagonal)
-  float* Hq_hi = nullptr;       // the same table as a double-FP32 pair: Hq = Hq_hi + Hq_lo
+  float* Hq_hi = nullptr;       // the same table as FP32 terms: Hq = Hq_hi + Hq_lo (48 bits) + Hq_lo2 (exact)
   float* Hq_lo = nullptr;
+  float* Hq_lo2 = nullptr;
   float Hq_hi_host[4 * 9] = {}; // host copies for k <= 4 (kernel parameters of the vector residual)
   float Hq_lo_host[4 * 9] = {};
+  float Hq_lo2_host[4 * 9] = {};
   int* band_lo = nullptr;
   int* band_hi = nullptr;
   float* Wf[2] = {nullptr, nullptr};            // FP32 copies: [0] = T^{-1}, [1] = T; n x n row-major
@@ -203,10 +205,13 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 // significant bits), u given as a double-FP32 pair (pitch Px, zero pads), f as
 // FP64 (pitch nx); r written as bf16 hi/lo at pitch Px with zero pads, or as
 // FP32 (out32).  Needs 1 <= k <= 8 and Dirichlet rows (returns
-// cudaErrorInvalidValue otherwise).
+// cudaErrorInvalidValue otherwise).  The rows of H enter as hi + lo FP32 pairs
+// (48 bits); with exact_coef also the third term lo2, which makes them exact:
+// a 48-bit operator is a different operator, whose solution a refinement with
+// only these residuals would converge to (off by ~kappa * 2^-48).
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
                               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s,
-                              float* out32 = nullptr, F16State* st = nullptr);
+                              float* out32 = nullptr, F16State* st = nullptr, bool exact_coef = false);
 // FP64 residual written as FP32 at pitch Px with its max |r| in state slot 0
 // (the F16X3 tier then splits it with launch_split_f16).  1 <= k <= 8.
 cudaError_t launch_stencil_f32out(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f,

@@ -113,9 +113,10 @@ def test_bf16x3_solve_matches_oracle(sem3d, i):
 @pytest.mark.parametrize("residual,sweeps", [("fp64", 3), ("mixed", 2), ("mixed", 4), ("df", 1), ("df", 3)])
 def test_bf16x3_residual_modes(sem3d, i, residual, sweeps):
     # Mixed: double-FP32 residuals for all sweeps but the last, which is FP64.
-    # df: every residual in double-FP32 (~48 bits): its 2^-48 error, amplified
-    # by the conditioning of the operator, leaves ~2e-12 at n=383 (measured):
-    # bound 1e-11, the reason the library's default keeps the last sweep FP64.
+    # df: every residual in double-FP32 (~48 bits, exact three-term rows of H):
+    # its 2^-48 error, amplified by the conditioning of the operator, leaves
+    # ~1.5e-12 at n=383 (measured): bound 1e-11, the reason the library's
+    # default keeps the last sweep FP64.
     n3, k, L3, c, (sx, sy, sz), F = _case(i)
     ref = refined_solve(F, sx, sy, sz, c, sweeps=1)
     with sem3d.Plan(*n3, k, L3, c) as p:
