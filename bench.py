@@ -309,6 +309,29 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "dmma_achieved_tflops": 2.0 * n**4 / (f64_ms / max(1, f64_n) / 1e3) / 1e12}
         plan.set_precision("bf16x3", args.sweeps)
 
+    # ---- FP32 CUDA-core tier (autotuned tiles) with FP64 refinement sweeps
+    fp32 = None
+    if args.fp32_steps > 0:
+        u_ex = torch.from_numpy(u_ex_h).cuda()
+        t0 = time.perf_counter()
+        plan.set_precision("fp32", args.fp32_sweeps)  # runs the autotuner for new pass shapes
+        tune_s = time.perf_counter() - t0
+        plan.profile(True)
+        ms_f = timed(step, args.fp32_steps, 1, stream, torch, dist)
+        f_n, f_ms = plan.profile_read("f32_mode_product")
+        plan.profile(False)
+        plan.sync_check(stream)
+        fp32 = {"path": "FP32 FFMA mode products (autotuned tiles) + FP64 refinement", "sweeps": args.fp32_sweeps,
+                "steps": args.fp32_steps, "warmup": 1, "ms_per_step": ms_f,
+                "value": job_throughput(dofs, world, ms_f) / 1e9, "unit": "GDoF/s", "autotune_s": tune_s,
+                "rel_linf_vs_exact_solution": float((u - u_ex).abs().max() / u_ex.abs().max()),
+                "rel_linf_vs_bf16x3": float((u - u_bf).abs().max() / u_bf.abs().max()),
+                "pass_avg_ms": f_ms / max(1, f_n),
+                "pass_tflops": 2.0 * n**4 / (f_ms / max(1, f_n) / 1e3) / 1e12,
+                "tiles": [plan.tuned_config(a) for a in range(3)]}
+        del u_ex
+        plan.set_precision("bf16x3", args.sweeps)
+
     # ---- TF32 tensor-core tier (the single-precision arithmetic of Table 10):
     # bare (0 sweeps) and with FP64 refinement sweeps
     tf32 = None
@@ -393,7 +416,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": t_setup},
         "accuracy": {"rel_linf_vs_exact_solution": err_exact, "rel_residual_linf": rel_res},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
-        "fp64_path": fp64, "tf32_path": tf32, "bf16x3_fp64_residuals": f64res, "bf16x3_df_residuals": dfres, "e2e": e2e,
+        "fp64_path": fp64, "fp32_path": fp32, "tf32_path": tf32, "bf16x3_fp64_residuals": f64res, "bf16x3_df_residuals": dfres, "e2e": e2e,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -507,6 +530,9 @@ def main():
     ap.add_argument("--fp64-residual-steps", type=int, default=3,
                     help="also time the BF16x3 path with FP64 residuals in every sweep (0 = skip)")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp32-steps", type=int, default=2,
+                    help="timed solves of the FP32 CUDA-core tier with --fp32-sweeps sweeps; 0 skips it")
+    ap.add_argument("--fp32-sweeps", type=int, default=2)
     ap.add_argument("--tf32-steps", type=int, default=5,
                     help="timed solves of the TF32 tier (bare, and refined with --tf32-sweeps); 0 skips it")
     ap.add_argument("--tf32-sweeps", type=int, default=7)

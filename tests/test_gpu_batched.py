@@ -54,7 +54,7 @@ def test_batched_matches_oracle(sem3d, mode):
                     for a in range(3):
                         p.set_tuned_config(a, (q + a) % 6)
             else:
-                p.set_precision(*[("fp32", 2), ("bf16x3", 3), ("fp64", 1)][q % 3])
+                p.set_precision(*[("fp32", 2), ("bf16x3", 3), ("fp64", 1), ("tf32", 5)][q % 4])
             plans.append(p)
             fs.append(torch.from_numpy(refs[q][0]).cuda())
             us.append(torch.full_like(fs[-1], float("nan")))

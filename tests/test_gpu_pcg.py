@@ -48,7 +48,7 @@ def _reference(case):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("prec,sweeps", [("fp64", 0), ("bf16x3", 1), ("bf16x3", 0)])
+@pytest.mark.parametrize("prec,sweeps", [("fp64", 0), ("bf16x3", 1), ("bf16x3", 0), ("tf32", 0)])
 def test_pcg_matches_direct_solve(sem3d, case, prec, sweeps):
     n3, k, rhs = CASES[case]
     V, F, ref = _reference(case)
