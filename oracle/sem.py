@@ -25,8 +25,8 @@ same order as the paper's vec(U) (Section 2.4).  Internally the paper's U(i,j,l)
 is the transposed view ``G.T`` of shape (nx, ny, nz).
 
 Homogeneous Dirichlet data are imposed by dropping the first and last global
-node of each axis (the "simple homogeneous Dirichlet treatment" the paper cites
-in Section 2.2); n = Ne*k - 1 interior nodes per axis.  This reading reproduces
+node of each axis (Section 2.2 leaves the Dirichlet treatment to an earlier
+paper); n = Ne*k - 1 interior nodes per axis.  This reading reproduces
 the DoF counts and the l2 errors of Table 1 (pinned in the tests).
 """
 
