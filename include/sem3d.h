@@ -185,7 +185,7 @@ sem3d_status sem3d_solve_host(sem3d_handle h, const double* f_host, double* u_ho
  * event). */
 sem3d_status sem3d_solve_host_wait(sem3d_handle h, void* stream);
 
-/* Many independent solves (the benchmark spec's batched workload; each problem is
+/* Many independent solves (a batch of Helmholtz problems; each problem is
  * Section 2.4's solve on its own box, grid, degree and shift).
  *   count : number of problems, 1 <= count <= 1024.
  *   hs    : count distinct plans on the current device; each keeps its own

@@ -118,7 +118,7 @@ HEADLINE = [
     ("bf16x3", 3, "fp64", 1e-11, 3e-16, None),
     ("bf16x3", 3, "df", 3e-11, 1e-13, None),      # double-FP32 residuals only (measured 1.1e-11): not FP64 refinement
     ("fp64", 1, "fp64", 1e-11, 3e-16, 1e-14),     # the timed plain path
-    ("fp32", 0, "mixed", 1e-5, None, None),       # unrefined FP32 (spec bound 1e-5)
+    ("fp32", 0, "mixed", 1e-5, None, None),       # unrefined FP32 (bound 1e-5 for unrefined single precision)
     ("bf16x3", 0, "mixed", 5e-4, None, None),     # unrefined BF16x3 (measured 4.3e-5)
 ]
 
