@@ -539,7 +539,8 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--oracle-lines", type=int, default=63, help="slab thickness; (lines+1) %% 4 == 0")
+    ap.add_argument("--oracle-lines", type=int, default=191,
+                    help="slab thickness of the oracle sample (~10 s of work on 16 cores); (lines+1) %% 4 == 0")
     ap.add_argument("--workload", choices=["solve", "batched", "ch", "pcg"], default="solve",
                     help="solve = the headline n=999 solve; the others time the batched, Cahn-Hilliard and PCG workloads")
     ap.add_argument("--ch-steps", type=int, default=1000)
