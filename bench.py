@@ -118,11 +118,12 @@ class ClockSampler:
 
 def oracle_sample(n: int, k: int, c: float, lines: int = 63):
     """Time the FP64 oracle (test infrastructure, numpy + BLAS on the host
-    cores) on a bounded sample of the n^3 workload: each of its mode products
-    along x, y and z and its H-form apply, run on `lines`-thick slabs of the
-    full-length grid lines.  Every grid line costs the same, so the time of
-    the oracle's refined solve of the whole grid (2 fast solves of 6 mode
-    products each + 1 apply) is the sum scaled by n / lines."""
+    cores) on a bounded sample of the n^3 workload: the operations of its
+    refined solve (two fast solves of six mode products and one division
+    each, one H-form apply), each run on `lines`-thick slabs of full-length
+    grid lines.  Every grid line costs the same, so the sample is `lines / n`
+    of the refined solve of the whole grid.  Returns (wall seconds of the
+    sample, DoF-equivalents it processed = lines * n^2)."""
     from oracle import sem_1d
     from oracle.sem import apply_h, mode_product
     s = sem_1d(k, (n + 1) // k, 0.0, 1.0)
@@ -130,44 +131,53 @@ def oracle_sample(n: int, k: int, c: float, lines: int = 63):
     rng = np.random.Generator(np.random.PCG64(7))
     slab_xy = rng.standard_normal((lines, n, n))          # (z, y, x): `lines` z-pages
     slab_z = rng.standard_normal((n, lines, n))           # `lines` y-rows, full z
-    t = {}
-    t0 = time.perf_counter(); mode_product(slab_xy.T, s.Tinv, 0); t["x"] = time.perf_counter() - t0
-    t0 = time.perf_counter(); mode_product(slab_xy.T, s.Tinv, 1); t["y"] = time.perf_counter() - t0
-    t0 = time.perf_counter(); mode_product(slab_z.T, s.Tinv, 2); t["z"] = time.perf_counter() - t0
     lam3 = s.lam[:, None, None] + s.lam[None, :, None] + s.lam[None, None, :lines] + c
-    t0 = time.perf_counter(); _ = slab_xy.T / lam3; t["div"] = time.perf_counter() - t0
-    t0 = time.perf_counter(); apply_h(slab_xy, s, s, s_lines, c); t["apply"] = time.perf_counter() - t0
-    scale = n / lines
-    solve = 2 * (t["x"] + t["y"] + t["z"]) + t["div"]
-    total = (2 * solve + t["apply"]) * scale
-    return total, sum(t.values())
+    t0 = time.perf_counter()
+    for _ in range(2):                                    # bare solve, then the refinement solve
+        mode_product(slab_z.T, s.Tinv, 2)
+        mode_product(slab_xy.T, s.Tinv, 1)
+        mode_product(slab_xy.T, s.Tinv, 0)
+        _ = slab_xy.T / lam3
+        mode_product(slab_xy.T, s.T, 0)
+        mode_product(slab_xy.T, s.T, 1)
+        mode_product(slab_z.T, s.T, 2)
+    apply_h(slab_xy, s, s, s_lines, c)                    # the sweep's residual
+    return time.perf_counter() - t0, float(lines) * n * n
+
+
+def oracle_cores() -> int:
+    return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
 
 
 def run_reference(args, rank: int, world: int):
+    """The oracle as the reference arm: each step is one bounded slab sample of
+    the n^3 refined solve, timed as it runs (no extrapolation): ms_per_step is
+    the sample's wall time and value its DoF-equivalents per second."""
     if rank != 0:
         return 0
     n, k, c = args.n, 4, 1.0
-    dofs = n**3
-    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
-    lines = args.oracle_lines
+    cores = oracle_cores()
+    lines = args.reference_lines
     for _ in range(args.warmup):
         oracle_sample(n, k, c, lines)
-    est, spent = [], 0.0
+    secs, units = [], 0.0
     for _ in range(args.steps):
-        e, sp = oracle_sample(n, k, c, lines)
-        est.append(e)
-        spent += sp
-    ms = float(np.mean(est)) * 1e3
-    value = dofs / (ms / 1e3) / 1e9
-    sample = (f"oracle (numpy/BLAS FP64) mode products along x, y, z and H-form apply on {lines}-line slabs "
-              f"of the n={n} grid; refined-solve time = (2 fast solves + 1 apply) x {n}/{lines}")
+        sec, u = oracle_sample(n, k, c, lines)
+        secs.append(sec)
+        units = u
+    ms = float(np.mean(secs)) * 1e3
+    value = units / (ms / 1e3) / 1e9
+    sample = (f"oracle (numpy/BLAS FP64) refined solve restricted to {lines}-line slabs of the n={n} grid: "
+              f"mode products along x, y, z (twice per fast solve, two fast solves) and one H-form apply, "
+              f"{units:.4g} DoF-equivalents per step ({lines}/{n} of one solve)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"q4_n{n}_expsine", "n": n, "k": k, "c": c, "dofs": dofs},
+        "config": {"workload": f"q4_n{n}_expsine", "n": n, "k": k, "c": c, "dofs": n**3,
+                   "dof_equivalents_per_step": units},
         "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle", "sample": sample,
-                         "cpu_seconds_per_step": spent / max(1, args.steps)},
+                         "seconds_per_step": ms / 1e3},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -175,6 +185,18 @@ def run_reference(args, rank: int, world: int):
 
 
 # --------------------------------------------------------------------- our path
+
+def single_gpu_only(gpus: int, world: int):
+    """Reason to refuse a run on more than one GPU, else None.  The tcgen05
+    mode-product kernels load the shared operand with TMA multicast inside
+    thread-block clusters; their tensor maps cover this GPU's memory only, and
+    the library is run one process on one GPU.  The solve does not shard
+    (replicas only), so a multi-GPU run would add nothing."""
+    if gpus != 1 or world != 1:
+        return (f"single GPU only (--gpus {gpus}, WORLD_SIZE {world}): the tensor-core kernels use cluster TMA "
+                "multicast and are run on one GPU per job")
+    return None
+
 
 def max_over_ranks(ms: float, dist, device: str) -> float:
     """The slowest rank's time (all ranks get it): the job's time for a weak-scaled
@@ -219,11 +241,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     from paper_2310_00226_gb300 import sem3d
     from paper_2310_00226_gb300.inputs import exp_sine
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist_mod
-        dist_mod.init_process_group("nccl")
-        dist = dist_mod
+    dist = None  # one GPU only: main() refuses more (see single_gpu_only)
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     peaks, peak_src = load_peaks()
@@ -246,10 +264,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     plan.sync_check(stream)
     clk = ClockSampler(local_rank)
     clk.start()
-    plan.profile(True)
     launches0 = plan.launch_count()
     ms = timed(step, args.steps, 0, stream, torch, dist)
     launches = plan.launch_count() - launches0
+    # Per-kernel device times come from a second timed region of the same K
+    # steps in which the library records an event pair around every launch on
+    # the launch's stream; the headline region above records none.
+    plan.profile(True)
+    ms_profiled = timed(step, args.steps, 0, stream, torch, dist)
     tc_n, tc_ms = plan.profile_read("tc_mode_product")
     per_pass = {}
     for key in ("tc_x", "tc_y", "tc_z", "tc_f64_out"):
@@ -388,7 +410,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "algorithmic_bytes_per_launch": 8.0 * ((n + 15) // 16 * 16) * n * n,
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": tc_avg_ms, "launches": tc_n,
-                "share_of_step": tc_ms / (ms * args.steps)}
+                "share_of_step": tc_ms / (ms_profiled * args.steps),
+                "kernel_times_from": (f"second timed region of {args.steps} steps with an event pair per launch "
+                                      f"({ms_profiled:.2f} ms per step there; headline region {ms:.2f} ms)")}
+    # The same fraction per unit of SM clock: the bench's median clock under load
+    # against the clock the peak was measured at (a power-capped GEMM runs slower
+    # clocks than a kernel that keeps the tensor pipe less busy).
+    peak_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if clocks.get("sm_mhz") and peak_mhz:
+        a_ghz, p_ghz = achieved / (clocks["sm_mhz"] / 1e3), peak / (peak_mhz / 1e3)
+        roofline["clock_normalised"] = {
+            "achieved_tflops_per_ghz": a_ghz, "peak_tflops_per_ghz": p_ghz, "frac": a_ghz / p_ghz,
+            "bench_sm_mhz_median": clocks["sm_mhz"], "peak_sm_mhz_median": peak_mhz,
+            "frac_of_nominal_dense_rate": achieved / (152 * 8192 * clocks["sm_mhz"] * 1e6 / 1e12),
+            "nominal_dense_rate": "8192 bf16 flop per clock per SM x 152 SMs x the bench's median SM clock"}
     kernels = {"tc_mode_product": {"launches": tc_n, "avg_ms": tc_avg_ms, "per_pass": per_pass},
                "stencil_residual": {"launches": st_n, "avg_ms": st_ms / max(1, st_n),
                                     "fp64_tflops": 2 * 21.0 * dofs / (st_ms / max(1, st_n) / 1e3) / 1e12},
@@ -397,12 +432,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_baseline:
-        est, spent = oracle_sample(n, k, c, args.oracle_lines)
-        cpu = {"value": dofs / est / 1e9, "unit": "GDoF/s", "ms_per_solve": est * 1e3,
-               "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
-               "sample": (f"oracle mode products along x, y, z and H-form apply on {args.oracle_lines}-line slabs "
-                          f"of the n={n} grid (refined solve = 2 fast solves + 1 apply, scaled by "
-                          f"{n}/{args.oracle_lines}); {spent:.1f} s of CPU work")}
+        sec, units = oracle_sample(n, k, c, args.oracle_lines)
+        cpu = {"value": units / sec / 1e9, "unit": "GDoF/s", "cores": oracle_cores(), "kind": "oracle",
+               "seconds": sec, "dof_equivalents": units,
+               "sample": (f"oracle refined solve restricted to {args.oracle_lines}-line slabs of the n={n} grid "
+                          f"(mode products along x, y, z and one H-form apply; {args.oracle_lines}/{n} of a "
+                          f"solve, {units:.4g} DoF-equivalents, {sec:.1f} s)")}
 
     line = {
         "metric": METRIC, "value": job_throughput(dofs, world, ms) / 1e9, "unit": "GDoF/s", "n_gpus": world,
@@ -520,7 +555,7 @@ def run_workload(args, rank: int):
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--gpus", type=int, default=1, help="must be 1: the library runs on one GPU")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -540,7 +575,9 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--oracle-lines", type=int, default=191,
-                    help="slab thickness of the oracle sample (~10 s of work on 16 cores); (lines+1) %% 4 == 0")
+                    help="slab thickness of the oracle CPU-baseline sample (~20 s on 16 cores); (lines+1) %% 4 == 0")
+    ap.add_argument("--reference-lines", type=int, default=63,
+                    help="slab thickness of each step of --impl reference (~4 s per step on 16 cores)")
     ap.add_argument("--workload", choices=["solve", "batched", "ch", "pcg"], default="solve",
                     help="solve = the headline n=999 solve; the others time the batched, Cahn-Hilliard and PCG workloads")
     ap.add_argument("--ch-steps", type=int, default=1000)
@@ -557,6 +594,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    refusal = single_gpu_only(args.gpus, world)
+    if refusal:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "n_gpus": max(args.gpus, world), "unavailable": refusal}), flush=True)
+        print(f"bench.py: {refusal}", file=sys.stderr, flush=True)
+        return 2
     if args.workload != "solve":
         return run_workload(args, rank)
     return run_ours(args, rank, world, local_rank)

@@ -343,9 +343,12 @@ sem3d_status sem3d_destroy(sem3d_handle h);
  *   SEM3D_ERR_INVALID_ARG with a message naming the limit.
  *   f, u : device FP64 arrays as in sem3d_solve; must not overlap.
  *   The current device must be the plan's device.  The first call on a device
- *   looks up the array's device address (cudaGetSymbolAddress), so make that
- *   first call before any stream capture.  No cudaMalloc, cudaFree or
- *   allocating library call is made.
+ *   (and the first after a cudaDeviceReset, which gives the array a new
+ *   address) looks up the array's device address (cudaGetSymbolAddress), so
+ *   make that first call before any stream capture.  No cudaMalloc, cudaFree,
+ *   event creation or other allocating call is made: the plan's own workspace
+ *   is neither allocated nor used, and sem3d_profile does not time these
+ *   launches (they are counted by sem3d_launch_count).
  *   All calls share the one array and leave their intermediates in it; calls
  *   whose work overlaps on the GPU (other streams, other threads, other plans
  *   on the same device) race on it and must be serialised by the caller. */

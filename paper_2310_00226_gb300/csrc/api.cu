@@ -2,6 +2,8 @@
 // one solve (Section 2.4, Eq. 13) plus FP64 iterative refinement.
 #include "sem3d_internal.h"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -1278,34 +1280,69 @@ static __device__ __align__(256) double g_static_scratch[3 * kStaticMaxDofs];
 
 std::mutex g_static_mu;
 constexpr int kMaxDevices = 64;
-double* g_static_ptr[kMaxDevices] = {};
+struct StaticAddr {
+  CUcontext ctx = nullptr;  // context the address belongs to
+  double* ptr = nullptr;
+};
+StaticAddr g_static_addr[kMaxDevices];
+
+// The driver's cuCtxGetCurrent, reached through the runtime's entry-point
+// query (the library links no driver library).
+CUresult current_context(CUcontext* ctx) {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &q, 4000, cudaEnableDefault, &r) == cudaSuccess &&
+        r == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(q);
+  });
+  return fn ? fn(ctx) : CUDA_ERROR_NOT_FOUND;
+}
 
 // Device address of g_static_scratch on device `dev` (which must be the
 // current device).  In host code the array's name is only a host-side
-// stand-in, so the address is asked from the runtime once per device.
+// stand-in, so the address is asked from the runtime: once per device and
+// CUDA context (after a cudaDeviceReset the device's new primary context
+// holds the array at a new address, which is looked up again).
 sem3d_status static_scratch(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(SEM3D_ERR_UNSUPPORTED, "device ordinal too large");
+  CUcontext ctx = nullptr;
+  if (current_context(&ctx) != CUDA_SUCCESS || ctx == nullptr)
+    return fail(SEM3D_ERR_CUDA, "sem3d_solve_fp64_static: no current CUDA context");
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  StaticAddr& a = g_static_addr[dev];
+  if (a.ptr == nullptr || a.ctx != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-    g_static_ptr[dev] = static_cast<double*>(p);
+    a.ptr = static_cast<double*>(p);
+    a.ctx = ctx;
   }
-  *out = g_static_ptr[dev];
+  *out = a.ptr;
   return SEM3D_OK;
 }
+
+// Launches of the allocation-free path are counted but never bracketed with
+// profiling events (creating an event may allocate).
+#define LAUNCH_COUNTED(plan, count, expr)                 \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);   \
+    (plan)->launches += (unsigned long long)(count);      \
+  } while (0)
 
 sem3d_status solve_once_f64_into(sem3d_plan* p, const double* in, double* out, bool accumulate, double* A, double* B,
                                  cudaStream_t s) {
   const Geom& g = p->g;
   const DevAxis* d = p->dev;
-  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].Tinv, in, A, EPI_STORE, nullptr, nullptr, nullptr, s));
-  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
-  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_DIV, d[0].lam, d[1].lam, d[2].lam, s));
-  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 2, d[2].T, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
-  LAUNCH(p, K_F64, 1, s, launch_mode_product_f64(g, 1, d[1].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
-  LAUNCH(p, K_F64, 1, s,
+  LAUNCH_COUNTED(p, 1, launch_mode_product_f64(g, 2, d[2].Tinv, in, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH_COUNTED(p, 1, launch_mode_product_f64(g, 1, d[1].Tinv, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH_COUNTED(p, 1, launch_mode_product_f64(g, 0, d[0].Tinv, B, A, EPI_DIV, d[0].lam, d[1].lam, d[2].lam, s));
+  LAUNCH_COUNTED(p, 1, launch_mode_product_f64(g, 2, d[2].T, A, B, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH_COUNTED(p, 1, launch_mode_product_f64(g, 1, d[1].T, B, A, EPI_STORE, nullptr, nullptr, nullptr, s));
+  LAUNCH_COUNTED(p, 1,
          launch_mode_product_f64(g, 0, d[0].T, A, out, accumulate ? EPI_ACCUM : EPI_STORE, nullptr, nullptr, nullptr, s));
   return SEM3D_OK;
 }
@@ -1333,7 +1370,7 @@ extern "C" sem3d_status sem3d_solve_fp64_static(sem3d_handle h, const double* f,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = solve_once_f64_into(h, f, u, false, A, B, s)) != SEM3D_OK) return st;
   for (int sw = 0; sw < h->sweeps; ++sw) {
-    LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+    LAUNCH_COUNTED(h, 1, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
     if ((st = solve_once_f64_into(h, r, u, true, A, B, s)) != SEM3D_OK) return st;
   }
   return SEM3D_OK;
