@@ -31,6 +31,8 @@ from .sem import (  # noqa: F401
     weak_matrix,
     schrodinger_solve,
     assembled_h3,
+    bdf2_history,
+    ch_explicit_term,
     ch_step,
 )
 from .tf32 import tf32_round, tf32_operand, fast_solve_rounded  # noqa: F401

@@ -366,6 +366,22 @@ def assembled_h3(sx: Sem1D, sy: Sem1D, sz: Sem1D) -> np.ndarray:
     return np.kron(Iz, np.kron(Iy, sx.H)) + np.kron(Iz, np.kron(sy.H, Ix)) + np.kron(sz.H, np.kron(Iy, Ix))
 
 
+def bdf2_history(phi_n: np.ndarray, phi_nm1: np.ndarray):
+    """History terms of the BDF2 step (Eq. 19): with a = 3/2, the time
+    derivative (a phi_{n+1} - phi_hat)/dt has phi_hat = 2 phi_n - phi_{n-1}/2,
+    and the nonlinear term is taken at the second-order extrapolation
+    phi_bar = 2 phi_n - phi_{n-1}.  Returns (phi_hat, phi_bar)."""
+    return 2.0 * phi_n - 0.5 * phi_nm1, 2.0 * phi_n - phi_nm1
+
+
+def ch_explicit_term(phi_bar: np.ndarray, eps: float, S: float) -> np.ndarray:
+    """g = (F'(phi_bar) - S phi_bar) / eps with F'(phi) = phi^3 - phi (the
+    derivative of F(phi) = (phi^2 - 1)^2 / 4, Section 3.5): the part of the
+    chemical potential treated explicitly, minus the stabilisation's explicit
+    half."""
+    return (phi_bar**3 - phi_bar - S * phi_bar) / eps
+
+
 def ch_step(phi_n: np.ndarray, phi_nm1: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Sem1D,
             eps: float, m: float, dt: float, S: float = 0.0) -> np.ndarray:
     """One BDF2 step of the Cahn-Hilliard system (Eq. 19, with the chemical
@@ -382,9 +398,8 @@ def ch_step(phi_n: np.ndarray, phi_nm1: np.ndarray, sx: Sem1D, sy: Sem1D, sz: Se
     """
     H3 = assembled_h3(sx, sy, sz)
     a = 1.5
-    phi_hat = 2.0 * phi_n - 0.5 * phi_nm1
-    phi_bar = 2.0 * phi_n - phi_nm1
-    g = (phi_bar**3 - phi_bar - S * phi_bar) / eps
+    phi_hat, phi_bar = bdf2_history(phi_n, phi_nm1)
+    g = ch_explicit_term(phi_bar, eps, S)
     P = a * np.eye(H3.shape[0]) + dt * m * (eps * H3 @ H3 + (S / eps) * H3)
     rhs = phi_hat.reshape(-1) - dt * m * (H3 @ g.reshape(-1))
     return np.linalg.solve(P, rhs).reshape(phi_n.shape)

@@ -379,3 +379,92 @@ def test_ch_step_nonlinear_term_and_energy_decay():
         prev, cur = cur, ch_step(cur, prev, s, s, s, eps, m, dt, S)
         energies.append(energy(cur))
     assert all(b < a for a, b in zip(energies, energies[1:])), energies
+
+
+# The BDF2 history (phi_hat, phi_bar) and the cubic term: pinned by a closed
+# form with distinct history levels and by convergence at order 2 to the
+# semi-discrete Cahn-Hilliard flow integrated by an independent stiff solver.
+
+def _ch_linear_limit_error(S: float) -> float:
+    # phi_n = a v, phi_{n-1} = b v (a != b) with v an eigenvector of H3 of
+    # eigenvalue L and amplitude small enough that the cube is negligible:
+    # phi_hat = (2a - b/2) v, phi_bar = (2a - b) v, g = -(1 + S)(2a - b) v / eps, so
+    # phi_{n+1} = [(2a - b/2) + dt m L (1 + S)(2a - b)/eps] / (3/2 + dt m (eps L^2 + S L/eps)) v.
+    from oracle import ch_step
+    sx, sy, sz = sem_1d(2, 3, 0.0, 1.0), sem_1d(1, 6, 0.0, 1.3), sem_1d(2, 2, 0.0, 0.7)
+    i, j, l = 2, 3, 1
+    v = 1e-9 * (sz.T[:, l][:, None, None] * sy.T[:, j][None, :, None] * sx.T[:, i][None, None, :])
+    L = sx.lam[i] + sy.lam[j] + sz.lam[l]
+    eps, m, dt = 0.05, 1.0, 1e-4
+    a, b = 1.0, -0.7
+    got = ch_step(a * v, b * v, sx, sy, sz, eps, m, dt, S)
+    factor = ((2 * a - b / 2) + dt * m * L * (1 + S) * (2 * a - b) / eps) / (1.5 + dt * m * (eps * L**2 + S * L / eps))
+    return float(np.abs(got - factor * v).max() / np.abs(factor * v).max())
+
+
+@pytest.mark.parametrize("S", [0.0, 2.0])
+def test_ch_step_linear_limit_with_distinct_history(S):
+    assert _ch_linear_limit_error(S) < 1e-9
+
+
+def _ch_flow_errors(S: float, steps=(10, 20, 40)):
+    """Max-norm errors at T of the BDF2 oracle with dt = T/N against the
+    semi-discrete flow phi' = -m H3 (eps H3 phi + (phi^3 - phi)/eps) (Eq. 17
+    with -Lap -> H3), integrated by scipy's Radau IIA at rtol 1e-12.  The
+    stabilisation adds (S/eps)(phi_{n+1} - phi_bar) = O(dt^2) and leaves the
+    limit unchanged.  The steps start from exact values phi_0, phi(dt)."""
+    from scipy.integrate import solve_ivp
+    from oracle import assembled_h3, ch_step
+    sx, sy, sz = sem_1d(2, 3, 0.0, 1.0), sem_1d(1, 4, 0.0, 1.0), sem_1d(2, 2, 0.0, 1.0)
+    H3 = assembled_h3(sx, sy, sz)
+    shape = (sz.n, sy.n, sx.n)
+    phi0 = 0.9 * np.random.Generator(np.random.PCG64(4)).uniform(-1, 1, shape)
+    eps, m, T = 0.2, 0.01, 0.02
+
+    def rhs(t, y):
+        return -m * (H3 @ (eps * (H3 @ y) + (y**3 - y) / eps))
+
+    def jac(t, y):
+        return -m * (H3 @ (eps * H3 + np.diag(3 * y**2 - 1) / eps))
+
+    sol = solve_ivp(rhs, (0.0, T), phi0.reshape(-1), method="Radau", rtol=1e-12, atol=1e-14, jac=jac,
+                    dense_output=True)
+    assert sol.success
+    ref = sol.y[:, -1]
+    assert np.abs(ref - phi0.reshape(-1)).max() > 0.5   # the flow moves: the cube matters
+    errs = []
+    for N in steps:
+        dt = T / N
+        prev, cur = phi0, sol.sol(dt).reshape(shape)
+        for _ in range(N - 1):
+            prev, cur = cur, ch_step(cur, prev, sx, sy, sz, eps, m, dt, S)
+        errs.append(float(np.abs(cur.reshape(-1) - ref).max()))
+    return errs
+
+
+@pytest.mark.parametrize("S", [0.0, 2.0])
+def test_ch_step_converges_to_the_semidiscrete_flow_at_order_2(S):
+    errs = _ch_flow_errors(S)
+    orders = [math.log2(errs[q] / errs[q + 1]) for q in range(len(errs) - 1)]
+    assert all(1.8 < o < 2.3 for o in orders), (errs, orders)
+    assert errs[-1] < 1e-3, errs
+
+
+@pytest.mark.parametrize("what", ["phi_bar_is_phi_n", "phi_hat_is_three_halves_phi_n", "dropped_cube"])
+def test_ch_pins_catch_planted_mistakes(what, monkeypatch):
+    import oracle.sem as osem
+    good_history, good_term = osem.bdf2_history, osem.ch_explicit_term
+    if what == "phi_bar_is_phi_n":
+        monkeypatch.setattr(osem, "bdf2_history", lambda pn, pm: (good_history(pn, pm)[0], pn))
+    elif what == "phi_hat_is_three_halves_phi_n":
+        monkeypatch.setattr(osem, "bdf2_history", lambda pn, pm: (1.5 * pn, good_history(pn, pm)[1]))
+    else:
+        monkeypatch.setattr(osem, "ch_explicit_term", lambda pb, eps, S: good_term(pb, eps, S) - pb**3 / eps)
+    caught_linear = _ch_linear_limit_error(2.0) > 1e-6
+    errs = _ch_flow_errors(2.0)
+    orders = [math.log2(errs[q] / errs[q + 1]) for q in range(len(errs) - 1)]
+    caught_flow = not (all(1.8 < o < 2.3 for o in orders) and errs[-1] < 1e-3)
+    if what == "dropped_cube":
+        assert caught_flow, errs          # invisible in the linear limit by construction
+    else:
+        assert caught_linear and caught_flow, (caught_linear, errs)
