@@ -145,6 +145,14 @@ def oracle_sample(n: int, k: int, c: float, lines: int = 63):
     return time.perf_counter() - t0, float(lines) * n * n
 
 
+def workload_config(n: int, k: int, c: float) -> dict:
+    """The `config` of both arms' JSON lines (the same workload)."""
+    return {"workload": f"q4_n{n}_expsine: Q^4, Ne={(n + 1) // k}/axis on [0,1]^3, n={n}, {n**3} DoF, "
+                        "-Lap u + u = f, u = e^x sin(pi x) sin(pi y) sin(pi z), Dirichlet",
+            "n": n, "k": k, "c": c, "dofs": n**3,
+            "l2": "inputs larger than L2 (8 GB FP64 per array at n=999)"}
+
+
 def oracle_cores() -> int:
     return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
 
@@ -174,8 +182,7 @@ def run_reference(args, rank: int, world: int):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"q4_n{n}_expsine", "n": n, "k": k, "c": c, "dofs": n**3,
-                   "dof_equivalents_per_step": units},
+        "config": workload_config(n, k, c), "dof_equivalents_per_step": units,
         "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "seconds_per_step": ms / 1e3},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -443,12 +450,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "metric": METRIC, "value": job_throughput(dofs, world, ms) / 1e9, "unit": "GDoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate) + f64 refinement", "data": "synthetic",
-        "config": {"workload": f"q4_n{n}_expsine: Q^4, Ne={(n + 1) // k}/axis on [0,1]^3, n={n}, {dofs} DoF, "
-                               "-Lap u + u = f, u = e^x sin(pi x) sin(pi y) sin(pi z), Dirichlet",
-                   "path": (f"tcgen05 BF16x3 mode products + {args.sweeps} refinement sweeps; residuals: "
-                            + ("double-FP32 except the last, FP64" if args.residual == "mixed" else "FP64")),
-                   "l2": "inputs larger than L2 (8 GB FP64 per array, 4 GB split-bf16 per pass)",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": t_setup},
+        "config": workload_config(n, k, c),
+        "path": (f"tcgen05 BF16x3 mode products + {args.sweeps} refinement sweeps; residuals: "
+                 + ("double-FP32 except the last, FP64" if args.residual == "mixed" else args.residual)),
+        "parallelism": "single GPU", "setup_s": t_setup,
         "accuracy": {"rel_linf_vs_exact_solution": err_exact, "rel_residual_linf": rel_res},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "fp64_path": fp64, "fp32_path": fp32, "tf32_path": tf32, "bf16x3_fp64_residuals": f64res, "bf16x3_df_residuals": dfres, "e2e": e2e,
@@ -459,6 +464,69 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     plan.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# --------------------------------------------------------------------- library GEMM peaks
+
+def probe_peaks(args):
+    """Dense GEMM rates of the vendor library on this GPU, as roofline
+    denominators for the tiers whose dtype MEASURED_PEAKS.json does not cover:
+    cuBLAS TF32 (torch.matmul on float32 with TF32 enabled), INT8 with INT32
+    accumulation (torch._int_mm), FP64 and, for reference, bf16.  Each is
+    timed with CUDA events as the best of 10 single calls (burst) and as the
+    mean over a ~2 s back-to-back loop (sustained), with nvidia-smi clocks
+    sampled during the loop.  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = "cuda"
+    res = {"probe": "library GEMM peaks", "n_gpus": 1, "gpu": torch.cuda.get_device_name(0)}
+
+    def run(label, make, mm, flops):
+        try:
+            a, b = make()
+            for _ in range(3):
+                mm(a, b)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(10):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mm(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            reps = max(3, int(2000.0 / best))
+            clk = ClockSampler(0)
+            clk.start()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                mm(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            clocks = clk.stop()
+            res[label] = {"burst_tflops": flops / best / 1e9, "sustained_tflops": flops / ms / 1e9,
+                          "burst_ms": best, "sustained_ms": ms, "reps": reps, "clocks": clocks}
+        except Exception as exc:  # noqa: BLE001 - reported, not hidden
+            res[label] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
+
+    n = 8192
+    torch.backends.cuda.matmul.allow_tf32 = True
+    run("tf32", lambda: (torch.randn(n, n, device=dev), torch.randn(n, n, device=dev)), torch.matmul, 2.0 * n**3)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    run("bf16", lambda: (torch.randn(n, n, device=dev, dtype=torch.bfloat16),
+                         torch.randn(n, n, device=dev, dtype=torch.bfloat16)), torch.matmul, 2.0 * n**3)
+    run("int8", lambda: (torch.randint(-128, 127, (n, n), device=dev, dtype=torch.int8),
+                         torch.randint(-128, 127, (n, n), device=dev, dtype=torch.int8)),
+        torch._int_mm, 2.0 * n**3)
+    m = 4096
+    run("fp64", lambda: (torch.randn(m, m, device=dev, dtype=torch.float64),
+                         torch.randn(m, m, device=dev, dtype=torch.float64)), torch.matmul, 2.0 * m**3)
+    res["unit"] = "TFLOP/s (TOP/s for int8)"
+    print(json.dumps(res), flush=True)
     return 0
 
 
@@ -576,8 +644,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--oracle-lines", type=int, default=191,
                     help="slab thickness of the oracle CPU-baseline sample (~20 s on 16 cores); (lines+1) %% 4 == 0")
-    ap.add_argument("--reference-lines", type=int, default=63,
-                    help="slab thickness of each step of --impl reference (~4 s per step on 16 cores)")
+    ap.add_argument("--reference-lines", type=int, default=31,
+                    help="slab thickness of each step of --impl reference (~5 s per step on 16 cores)")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="time the vendor library's TF32, bf16, INT8 and FP64 GEMMs (roofline denominators) and exit")
     ap.add_argument("--workload", choices=["solve", "batched", "ch", "pcg"], default="solve",
                     help="solve = the headline n=999 solve; the others time the batched, Cahn-Hilliard and PCG workloads")
     ap.add_argument("--ch-steps", type=int, default=1000)
@@ -594,6 +664,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.probe_peaks:
+        return probe_peaks(args) if world == 1 else 2
     refusal = single_gpu_only(args.gpus, world)
     if refusal:
         if rank == 0:
