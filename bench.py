@@ -263,7 +263,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     u = torch.empty_like(f)
 
     # ---- headline: BF16x3 + FP64 refinement sweeps
+    if args.tc_config != "auto":  # pin the tensor-core kernel (else set_precision measures both)
+        for ax in range(3):
+            plan.set_tc_config(ax, int(args.tc_config))
+    t_tune = time.perf_counter()
     plan.set_precision("bf16x3", args.sweeps)
+    t_tune = time.perf_counter() - t_tune
+    tc_variant = [plan.tc_config(ax) for ax in range(3)]
     plan.set_residual(args.residual)
     step = lambda: plan.solve(f, u, stream)  # noqa: E731
     for _ in range(args.warmup):
@@ -366,11 +372,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     tf32 = None
     if args.tf32_steps > 0:
         u_ex = torch.from_numpy(u_ex_h).cuda()
-        # TF32 dense peak: the measured sustained bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25 PF/s)
-        tf32_peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])) * 1.1 / 2.25
+        # TF32 dense peak: cuBLAS TF32 measured on this GPU (sustained loop, profiles/library_gemm_peaks.json),
+        # else the measured sustained bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25 PF/s)
+        tf32_peak, tf32_src = None, None
+        try:
+            with open(os.path.join(ROOT, "profiles", "library_gemm_peaks.json")) as fh:
+                tf32_peak = float(json.load(fh)["tf32"]["sustained"])
+            tf32_src = "cuBLAS TF32 GEMM, sustained, measured on GB300 (profiles/library_gemm_peaks.json)"
+        except (OSError, ValueError, KeyError):
+            tf32_peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])) * 1.1 / 2.25
+            tf32_src = f"{peak_src} bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16 ratio)"
         tf32 = {"path": "tcgen05 kind::tf32 mode products (rotating K-major layouts)", "steps": args.tf32_steps,
-                "warmup": 1, "tf32_peak_tflops": tf32_peak,
-                "tf32_peak_source": f"{peak_src} bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16 ratio)"}
+                "warmup": 1, "tf32_peak_tflops": tf32_peak, "tf32_peak_source": tf32_src}
         for label, sw in (("bare", 0), ("refined", args.tf32_sweeps)):
             plan.set_precision("tf32", sw)
             plan.profile(True)
@@ -454,6 +467,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "path": (f"tcgen05 BF16x3 mode products + {args.sweeps} refinement sweeps; residuals: "
                  + ("double-FP32 except the last, FP64" if args.residual == "mixed" else args.residual)),
         "parallelism": "single GPU", "setup_s": t_setup,
+        "tc_kernel": {"per_axis": tc_variant, "legend": "0 = one CTA per 128x256 tile (W multicast in clusters of 4), "
+                      "1 = cta_group::2 CTA pair per 256x256 tile", "chosen_by": "autotuner" if args.tc_config == "auto"
+                      else "pinned", "set_precision_s": t_tune},
         "accuracy": {"rel_linf_vs_exact_solution": err_exact, "rel_residual_linf": rel_res},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "fp64_path": fp64, "fp32_path": fp32, "tf32_path": tf32, "bf16x3_fp64_residuals": f64res, "bf16x3_df_residuals": dfres, "e2e": e2e,
@@ -569,9 +585,28 @@ def run_workload(args, rank: int):
             ms = _timed_host(lambda: sem3d.solve_batched(plans, fs, us, stream), args.steps, args.warmup, torch)
             plans[0].sync_check(stream)
             res[prec] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": sweeps,
-                         "path": "grouped launches" if prec == "fp32" else "stream pool"}
+                         "path": ("grouped FP32 launch per pass" if prec == "fp32" else
+                                  "grouped tcgen05 CTA-pair launch per pass (tile queue over all problems)")}
+        # the same BF16x3 solves issued per plan on a pool of 8 streams (no grouping), for comparison
+        pool = [torch.cuda.Stream() for _ in range(8)]
+
+        def per_plan():
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            for q, p in enumerate(plans):
+                pool[q % 8].wait_event(ev)
+                p.solve(fs[q], us[q], pool[q % 8])
+            for st in pool:
+                e2 = torch.cuda.Event()
+                e2.record(st)
+                stream.wait_event(e2)
+
+        ms = _timed_host(per_plan, args.steps, args.warmup, torch)
+        plans[0].sync_check(stream)
+        res["bf16x3_per_plan_streams"] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": 3,
+                                          "path": "each plan's sem3d_solve on a pool of 8 streams"}
         line.update({"metric": f"{args.batch_count} batched Helmholtz solves (uneven n in {{63..511}}, k in {{2,3,4,6}}): GDoF/s",
-                     "value": res["fp32"]["GDoF_per_s"], "unit": "GDoF/s", "total_dofs": dofs, "tiers": res,
+                     "value": res["bf16x3"]["GDoF_per_s"], "unit": "GDoF/s", "total_dofs": dofs, "tiers": res,
                      "steps": args.steps, "warmup": args.warmup})
     elif args.workload == "ch":
         n, k = args.workload_n or 511, 2
@@ -646,6 +681,8 @@ def main():
                     help="slab thickness of the oracle CPU-baseline sample (~20 s on 16 cores); (lines+1) %% 4 == 0")
     ap.add_argument("--reference-lines", type=int, default=31,
                     help="slab thickness of each step of --impl reference (~5 s per step on 16 cores)")
+    ap.add_argument("--tc-config", choices=["auto", "0", "1"], default="auto",
+                    help="tensor-core kernel of the headline: autotuned, 0 = one CTA per tile, 1 = CTA pair")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="time the vendor library's TF32, bf16, INT8 and FP64 GEMMs (roofline denominators) and exit")
     ap.add_argument("--workload", choices=["solve", "batched", "ch", "pcg"], default="solve",

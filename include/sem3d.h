@@ -313,6 +313,27 @@ sem3d_status sem3d_tuned_config(sem3d_handle h, int axis, int* config);
  * the next pin; sem3d_set_precision does not re-measure a known shape). */
 sem3d_status sem3d_set_tuned_config(sem3d_handle h, int axis, int config);
 
+/* Tensor-core kernel of this plan's mode product along `axis` (0 = x, 1 = y,
+ * 2 = z) in the SEM3D_BF16X3, SEM3D_BF16 and SEM3D_TF32 tiers (SEM3D_F16X3
+ * always uses 0):
+ *   0 = one CTA per 128-row x 256-output tile, the W tile multicast by TMA
+ *       across clusters of 4 CTAs, 4 pipeline stages;
+ *   1 = one cta_group::2 MMA per pair of SMs on 256 x 256 tiles, each CTA of
+ *       the pair staging its 128 rows and half of the W tile, 6 stages.
+ * Both compute the same products in the same order (bit-identical results).
+ * sem3d_set_precision(h, SEM3D_BF16X3, SEM3D_BF16 or SEM3D_TF32, ...) times
+ * both on a synthetic pass of each pass shape the process has not measured
+ * before (synchronous; up to 512 MB of scratch, freed again) and keeps the
+ * faster one in a process-wide table (split tiers: keyed by axis, nx, ny, nz
+ * and products per pass; TF32: by the pass's contracted length and its two
+ * row extents).  sem3d_tc_config reports the choice for the plan's current
+ * tier (0 for a shape never measured); sem3d_set_tc_config pins `config` (0
+ * or 1) for this plan's pass along `axis` in all three tiers, for every plan
+ * of the process with that shape (sem3d_set_precision does not re-measure a
+ * known shape). */
+sem3d_status sem3d_tc_config(sem3d_handle h, int axis, int* config);
+sem3d_status sem3d_set_tc_config(sem3d_handle h, int axis, int config);
+
 /* Failure-detection testing (no counterpart in the paper).  The next
  * `launches` tensor-core kernel launches of the process (any plan) issue no
  * operand loads: their bounded waits (1 s each, on mbarriers that nothing then

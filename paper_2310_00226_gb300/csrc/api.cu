@@ -479,6 +479,10 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweep
     const cudaError_t e = f32_autotune(h->g, h->dev);
     if (e != cudaSuccess) return fail(SEM3D_ERR_CUDA, std::string("FP32 autotuning: ") + cudaGetErrorString(e));
   }
+  if (prec == SEM3D_BF16X3 || prec == SEM3D_BF16) {
+    const cudaError_t e = tc_autotune(h->g, h->dev, prec == SEM3D_BF16 ? 1 : 3, h->d_err, h->num_sms);
+    if (e != cudaSuccess) return fail(SEM3D_ERR_CUDA, std::string("tensor-core autotuning: ") + cudaGetErrorString(e));
+  }
   h->prec = prec;
   h->sweeps = sweeps;
   return SEM3D_OK;
@@ -503,6 +507,29 @@ sem3d_status sem3d_tuned_config(sem3d_handle h, int axis, int* config) {
   if (!h || !config) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
   if (axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
   *config = f32_config(axis, h->g);
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_set_tc_config(sem3d_handle h, int axis, int config) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  if (axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
+  if (config != TC_SINGLE && config != TC_PAIR) return fail(SEM3D_ERR_INVALID_ARG, "config must be 0 or 1");
+  tc_set_config(axis, h->g, 1, config);
+  tc_set_config(axis, h->g, 3, config);
+  const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+  tf32_set_config(n3[axis], n3[(axis + 1) % 3], n3[(axis + 2) % 3], config);
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_tc_config(sem3d_handle h, int axis, int* config) {
+  if (!h || !config) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  if (axis < 0 || axis > 2) return fail(SEM3D_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
+  if (h->prec == SEM3D_TF32) {
+    const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+    *config = tf32_config(n3[axis], n3[(axis + 1) % 3], n3[(axis + 2) % 3]);
+  } else {
+    *config = tc_config(axis, h->g, h->prec == SEM3D_BF16 ? 1 : 3);
+  }
   return SEM3D_OK;
 }
 
@@ -1176,6 +1203,146 @@ sem3d_status batched_f32(int count, const sem3d_handle* hs, const double* const*
 
 // Any tiers: each problem's own solve on a pool of streams, forked from and
 // joined back to the caller's stream.
+// Double-FP32 sweeps of a plan's split-tier solve (see run_solve): 0 when its
+// residuals are all FP64.
+int df_sweeps(const sem3d_plan* h) {
+  const bool df_ok = h->k <= 8 && h->g.bc == 0 && (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_F16X3);
+  const int sw = h->sweeps;
+  return !df_ok ? 0 : (h->residual == SEM3D_RESIDUAL_MIXED && sw >= 2) ? sw - 1
+                    : (h->residual == SEM3D_RESIDUAL_DF) ? sw : 0;
+}
+
+// Fork `count` per-problem tasks from s onto the batch's stream pool and join
+// them back into s (events created once per batched call).
+struct StreamFan {
+  cudaStream_t s;
+  int ns;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[8] = {};
+  ~StreamFan() {
+    if (fork) cudaEventDestroy(fork);
+    for (auto e : join)
+      if (e) cudaEventDestroy(e);
+  }
+  sem3d_status init(cudaStream_t s_, int count) {
+    s = s_;
+    ns = count < 8 ? count : 8;
+    CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int k = 0; k < ns; ++k) CUDA_TRY(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+    return SEM3D_OK;
+  }
+  sem3d_status begin() {
+    CUDA_TRY(cudaEventRecord(fork, s));
+    for (int k = 0; k < ns; ++k) CUDA_TRY(cudaStreamWaitEvent(g_batch.streams[k], fork, 0));
+    return SEM3D_OK;
+  }
+  cudaStream_t stream(int q) const { return g_batch.streams[q % ns]; }
+  sem3d_status end() {
+    for (int k = 0; k < ns; ++k) {
+      CUDA_TRY(cudaEventRecord(join[k], g_batch.streams[k]));
+      CUDA_TRY(cudaStreamWaitEvent(s, join[k], 0));
+    }
+    return SEM3D_OK;
+  }
+};
+
+// All plans in a split tier (BF16x3 or BF16) with the same sweeps and the same
+// residual schedule: each of the six mode-product passes of every solve of the
+// refinement runs as ONE persistent CTA-pair launch over all problems (a queue
+// of pair tiles with prefix offsets; per-problem tensor maps and epilogue
+// arguments in a device table).  The splits and residuals, which are
+// element-wise per problem, run on the stream pool between them.
+sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* f, double* const* u, cudaStream_t s) {
+  const int sweeps = hs[0]->sweeps;
+  const int ndf = df_sweeps(hs[0]);
+  const int nprod = hs[0]->prec == SEM3D_BF16 ? 1 : 3;
+  sem3d_status st = batch_resources(hs[0]->device, 6 * (size_t)(1 + sweeps));
+  if (st != SEM3D_OK) return st;
+  StreamFan fan;
+  if ((st = fan.init(s, count)) != SEM3D_OK) return st;
+  std::vector<TcBuffers> S0(count), S1(count);
+  std::vector<DfBuffers> D(count);
+  for (int q = 0; q < count; ++q) {
+    sem3d_plan* h = hs[q];
+    const size_t Ns = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(__nv_bfloat16));
+    const size_t Nf = align256((size_t)h->g.Px * h->g.ny * h->g.nz * sizeof(float));
+    char* w = static_cast<char*>(h->ws);
+    S0[q] = TcBuffers{reinterpret_cast<__nv_bfloat16*>(w), reinterpret_cast<__nv_bfloat16*>(w + Ns)};
+    S1[q] = TcBuffers{reinterpret_cast<__nv_bfloat16*>(w + 2 * Ns), reinterpret_cast<__nv_bfloat16*>(w + 3 * Ns)};
+    D[q] = DfBuffers{reinterpret_cast<float*>(w + 6 * Ns), reinterpret_cast<float*>(w + 6 * Ns + Nf)};
+  }
+  const DfBuffers none{nullptr, nullptr};
+  std::vector<TcGroupItem> items(count);
+  size_t stage = 0;
+  // One grouped pass: problem q reads in(q), writes out(q) / out64(q) / df(q).
+  auto pass = [&](int axis, int which, int epi, int sub, auto in_of, auto out_of, auto out64_of,
+                  bool use_df) -> sem3d_status {
+    for (int q = 0; q < count; ++q) {
+      const sem3d_plan* h = hs[q];
+      items[q] = TcGroupItem{&h->g, &h->dev[axis], in_of(q), out_of(q), out64_of(q), use_df ? D[q] : none,
+                             h->dev[0].lamf, h->dev[1].lamf, h->dev[2].lamf};
+    }
+    char* ht = static_cast<char*>(g_batch.host_table) + stage * kStageTableBytes;
+    char* dt = static_cast<char*>(g_batch.dev_table) + stage * kStageTableBytes;
+    ++stage;
+    LAUNCH_SUB(hs[0], K_TC, sub, 1, s,
+               launch_mode_product_bf16x3_grouped(count, items.data(), axis, which, epi, nprod, hs[0]->d_err, dt, ht,
+                                                  kStageTableBytes, hs[0]->num_sms, s));
+    return SEM3D_OK;
+  };
+  auto s0 = [&](int q) { return S0[q]; };
+  auto s1 = [&](int q) { return S1[q]; };
+  auto no64 = [&](int) -> double* { return nullptr; };
+  // Forward z, y, x (division fused), backward x, y, then the last z pass with
+  // the epilogue epi_last into u / the double-FP32 solution.
+  auto solve_group = [&](int epi_last, bool out_u, bool use_df) -> sem3d_status {
+    sem3d_status r;
+    if ((r = pass(2, 0, EPI_STORE, K_TC_Z, s0, s1, no64, false)) != SEM3D_OK) return r;
+    if ((r = pass(1, 0, EPI_STORE, K_TC_Y, s1, s0, no64, false)) != SEM3D_OK) return r;
+    if ((r = pass(0, 0, EPI_DIV, K_TC_X, s0, s1, no64, false)) != SEM3D_OK) return r;
+    if ((r = pass(0, 1, EPI_STORE, K_TC_X, s1, s0, no64, false)) != SEM3D_OK) return r;
+    if ((r = pass(1, 1, EPI_STORE, K_TC_Y, s0, s1, no64, false)) != SEM3D_OK) return r;
+    return pass(2, 1, epi_last, K_TC_F64OUT, s1, s0, [&](int q) -> double* { return out_u ? u[q] : nullptr; },
+                use_df);
+  };
+  // f -> split input of every problem
+  if ((st = fan.begin()) != SEM3D_OK) return st;
+  for (int q = 0; q < count; ++q)
+    LAUNCH(hs[q], K_SPLIT, 1, fan.stream(q), launch_split(hs[q]->g, f[q], S0[q].hi, S0[q].lo, fan.stream(q)));
+  if ((st = fan.end()) != SEM3D_OK) return st;
+  if (ndf == 0) {
+    if ((st = solve_group(EPI_STORE, true, false)) != SEM3D_OK) return st;
+  } else {
+    if ((st = solve_group(EPI_DF_STORE, false, true)) != SEM3D_OK) return st;
+    const bool exact_coef = hs[0]->residual == SEM3D_RESIDUAL_DF;
+    for (int sw = 1; sw <= ndf; ++sw) {
+      if ((st = fan.begin()) != SEM3D_OK) return st;
+      for (int q = 0; q < count; ++q) {
+        sem3d_plan* h = hs[q];
+        const int launches = (h->k == 1 || h->k == 2 || h->k == 4 || h->g.Px == h->g.nx) ? 1 : 2;
+        LAUNCH(h, K_STENCIL, launches, fan.stream(q),
+               launch_stencil_df(h->g, h->k, h->dev, D[q], f[q], S0[q].hi, S0[q].lo, fan.stream(q), nullptr, nullptr,
+                                 exact_coef));
+      }
+      if ((st = fan.end()) != SEM3D_OK) return st;
+      const bool last_df = sw == ndf;
+      if ((st = solve_group(last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, last_df, true)) != SEM3D_OK) return st;
+    }
+  }
+  for (int sw = ndf; sw < sweeps; ++sw) {
+    if ((st = fan.begin()) != SEM3D_OK) return st;
+    for (int q = 0; q < count; ++q) {
+      sem3d_plan* h = hs[q];
+      LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, fan.stream(q),
+             launch_stencil(h->g, h->k, h->dev, u[q], f[q], nullptr, S0[q].hi, S0[q].lo, 2, fan.stream(q)));
+    }
+    if ((st = fan.end()) != SEM3D_OK) return st;
+    if ((st = solve_group(EPI_ACCUM, true, false)) != SEM3D_OK) return st;
+  }
+  CUDA_TRY(cudaEventRecord(g_batch.done, s));
+  return SEM3D_OK;
+}
+
 sem3d_status batched_streams(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
                              cudaStream_t s) {
   sem3d_status st = batch_resources(hs[0]->device, 1);
@@ -1227,11 +1394,18 @@ sem3d_status sem3d_solve_batched(int count, const sem3d_handle* hs, const double
     if (st != SEM3D_OK) return st;
   }
   std::lock_guard<std::mutex> lk(g_batch.mu);
-  bool grouped = count <= 64;
-  for (int q = 0; q < count && grouped; ++q)
-    grouped = hs[q]->prec == SEM3D_FP32 && hs[q]->sweeps == hs[0]->sweeps;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return grouped ? batched_f32(count, hs, f, u, s) : batched_streams(count, hs, f, u, s);
+  bool grouped_f32 = count <= 64, grouped_tc = count <= 64;
+  for (int q = 0; q < count; ++q) {
+    const sem3d_plan* h = hs[q];
+    grouped_f32 = grouped_f32 && h->prec == SEM3D_FP32 && h->sweeps == hs[0]->sweeps;
+    grouped_tc = grouped_tc && (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_BF16) && h->prec == hs[0]->prec &&
+                 h->sweeps == hs[0]->sweeps && df_sweeps(h) == df_sweeps(hs[0]) &&
+                 h->residual == hs[0]->residual;
+  }
+  if (grouped_f32) return batched_f32(count, hs, f, u, s);
+  if (grouped_tc) return batched_tc(count, hs, f, u, s);
+  return batched_streams(count, hs, f, u, s);
 }
 
 sem3d_status sem3d_destroy(sem3d_handle h) {

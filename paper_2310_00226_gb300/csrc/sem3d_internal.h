@@ -235,6 +235,42 @@ void tc_inject_stall(int launches);
 // Takes one launch from the pending sem3d_inject_stall count: 1 if this
 // launch must run with its producer stalled, else 0.
 int tc_take_stall();
+// Replace the pending stall count (returns the old one): autotuners measure
+// with no stall pending and put the count back afterwards.
+int tc_swap_stall(int launches);
+// Tensor-core kernel variant of the BF16x3 / BF16 mode products, per pass
+// shape (process-wide): TC_SINGLE = one CTA per 128 x 256 tile with W
+// multicast in clusters of 4; TC_PAIR = one cta_group::2 MMA per pair of SMs
+// on 256 x 256 tiles.  Keyed by (axis, grid shape, products per pass: 3 for
+// BF16x3, 1 for BF16).  tc_autotune measures both on each pass shape of g not
+// measured before (synchronous; scratch of up to 2^26 elements per split
+// array) and keeps the faster; tc_set_config pins one.
+enum { TC_SINGLE = 0, TC_PAIR = 1 };
+int tc_config(int axis, const Geom& g, int nprod);
+bool tc_config_known(int axis, const Geom& g, int nprod);
+void tc_set_config(int axis, const Geom& g, int nprod, int cfg);
+cudaError_t tc_autotune(const Geom& g, const DevAxis* ax, int nprod, int* err_flag, int num_sms);
+// One problem of a grouped BF16x3 / BF16 pass (tc_pair_kernels.cu): its grid,
+// the axis data of the pass's axis, split input / output (or FP64 out64, or
+// the double-FP32 solution df for the double-FP32 modes) and lambda vectors.
+struct TcGroupItem {
+  const Geom* g;
+  const DevAxis* W;
+  TcBuffers in, out;
+  double* out64;
+  DfBuffers df;
+  const float *lamx, *lamy, *lamz;
+};
+// Bytes of the device (and pinned host) table of a grouped launch.
+size_t tc_group_table_bytes(int count);
+// The same mode product (axis, which = 0: T^{-1}, 1: T; one epilogue mode for
+// all) of `count` problems as ONE persistent CTA-pair launch: the problems'
+// tensor maps and arguments are written to host_table (pinned, 64-byte
+// aligned, >= tc_group_table_bytes(count)), copied to dev_table on s, and the
+// kernel walks one queue of pair tiles over all problems.
+cudaError_t launch_mode_product_bf16x3_grouped(int count, const TcGroupItem* items, int axis, int which, int epi,
+                                               int nprod, int* err_flag, void* dev_table, void* host_table,
+                                               size_t table_bytes, int num_sms, cudaStream_t s);
 
 // One TF32 mode product of the rotating-layout solve (tf32_kernels.cu): the
 // input has dims (nK, d1, d2), nK fastest at row pitch P0 (a multiple of 4);
@@ -255,6 +291,13 @@ struct Tf32Pass {
   float c = 0.f;
 };
 cudaError_t launch_mode_product_tf32(const Tf32Pass& p, int* err_flag, int num_sms, cudaStream_t s);
+// Kernel variant (TC_SINGLE / TC_PAIR) of the TF32 pass of shape (nK, d1, d2),
+// process-wide, as for the split tiers; tf32_autotune measures the three pass
+// shapes of g not measured before (synchronous; up to 512 MB scratch).
+int tf32_config(int nK, int d1, int d2);
+bool tf32_config_known(int nK, int d1, int d2);
+void tf32_set_config(int nK, int d1, int d2, int cfg);
+cudaError_t tf32_autotune(const Geom& g, const DevAxis* ax, int* err_flag, int num_sms);
 // FP64 x-fastest array (pitch nx) -> TF32-rounded FP32 at pitch g.Px.
 cudaError_t launch_to_tf32(const Geom& g, const double* in, float* out, cudaStream_t s);
 cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,

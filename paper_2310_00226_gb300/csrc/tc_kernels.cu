@@ -28,322 +28,20 @@
 // overlaps the MMAs of the next.  Every wait is bounded: on expiry the kernel
 // records SEM3D_ERR_TIMEOUT in *err, drains its own copies and MMAs, frees
 // TMEM and returns.
-#include "sem3d_internal.h"
-#include "tc_ptx.cuh"
+#include "tc_common.cuh"
 
+#include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace sem3d {
 
+
 namespace {
 
-constexpr int BM = 128;           // tile rows = TMEM lanes
-constexpr int BN = 256;           // tile outputs = TMEM columns per accumulator
-constexpr int BK = 32;            // K per stage: one 64-byte swizzle row of bf16 (K-major tiles)
-constexpr int STAGES = 4;
-constexpr int A_TILE_BYTES = BM * BK * 2;  // 8 KB
-constexpr int B_TILE_BYTES = BN * BK * 2;  // 16 KB
-constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
-// x-pass split outputs are staged per epilogue warp (32 rows x 64 bytes, rows
-// padded to 80 bytes so that 16-byte accesses of 8 lanes hit distinct banks)
-// and written back row-contiguously; see epilogue_chunk.
-constexpr int XSTAGE_ROW = 80, XSTAGE_BYTES = 32 * XSTAGE_ROW;
-__host__ __device__ constexpr int smem_bytes(int pass) {
-  return STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + (pass == 0 ? 8 * XSTAGE_BYTES : 0);
-}
-constexpr int TMEM_COLS = 2 * BN;  // 512
-// Epilogue warps: two per TMEM lane quadrant for the split-bf16 outputs; four
-// for the outputs that read and write FP64 / double-FP32 solution arrays
-// (12-16 more bytes per element), which need more loads in flight to keep up
-// with the MMAs.  Threads: producer warp, MMA warp, epilogue warps.
-__host__ __device__ constexpr int epi_warps(int mode) { return mode >= 2 ? 16 : 8; }
-__host__ __device__ constexpr int num_threads(int mode) { return 64 + 32 * epi_warps(mode); }
-
-// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
-// B format at bits 7-9 and 10-12 (0 = fp16, 1 = bf16; both operands of one
-// MMA always share the format), A major-ness at bit 15 (1 = MN-major),
-// B K-major, N>>3 at bits 17-22, M>>4 at bits 24-28.
-__host__ __device__ constexpr uint32_t make_idesc(int m, int n, bool a_mn_major, int fmt) {
-  return (1u << 4) | ((fmt == 1 ? 0u : 1u) << 7) | ((fmt == 1 ? 0u : 1u) << 10) | ((a_mn_major ? 1u : 0u) << 15) |
-         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// ---------------------------------------------------------------- kernel
-
-struct TcArgs {
-  int m_tiles, n_tiles, batches, k_blocks;
-  int kc;              // K blocks per TMEM accumulation chunk (see the kernel)
-  int rows;            // valid tile rows per batch (x: ny*nz, y: Px, z: Px*ny)
-  int nout;            // valid outputs (length of the output axis)
-  int nx, ny, nz, Px;
-  __nv_bfloat16* out_hi;
-  __nv_bfloat16* out_lo;
-  double* out64;
-  float* df_hi;        // solution in double-FP32 form (hi + lo), dense n-pitch
-  float* df_lo;
-  const float *lamx, *lamy, *lamz;
-  float c;
-  int* err;
-  // F16X3 scaling (FMT = 1): state slots read / written, W scale exponent,
-  // infinity norm of W and the division bound (see F16Pass).
-  F16State* st;
-  int pin, pout, eW;
-  float normW, div_bound;
-  int stall;           // failure-detection test: the producer issues no loads, so the waits expire
-};
-
-// Output modes of the epilogue.  The DF modes (y and z passes only) keep the
-// solution as a double-FP32 pair u = hi + lo between refinement sweeps:
-//   OUT_DF_STORE     : (hi, lo) = (acc, 0)
-//   OUT_DF_ACCUM     : (hi, lo) += acc           (compensated FP32 addition)
-//   OUT_DF_ACCUM_F64 : out64 = (double)hi + (double)lo, (hi, lo) = (hi, lo) + acc
-enum : int {
-  OUT_SPLIT = 0, OUT_DIV_SPLIT = 1, OUT_F64 = 2, OUT_F64_ACCUM = 3,
-  OUT_DF_STORE = 4, OUT_DF_ACCUM = 5, OUT_DF_ACCUM_F64 = 6
-};
-
-// Split two FP32 values into bf16 hi + lo pairs (packed bf16x2: element 0 in
-// the low half).  hi = rn(v), lo = rn(v - hi).
-__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(v1), "f"(v0));
-  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(v1 - h1), "f"(v0 - h0));
-}
-
-// Split two FP32 values into fp16 hi + lo pairs (packed f16x2, element 0 in
-// the low half): hi = rn(v), lo = rn(v - hi).
-__device__ __forceinline__ void split_pair_f16(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(v1), "f"(v0));
-  const float h0 = __half2float(__ushort_as_half((unsigned short)(hi & 0xFFFFu)));
-  const float h1 = __half2float(__ushort_as_half((unsigned short)(hi >> 16)));
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(v1 - h1), "f"(v0 - h0));
-}
-
-template <int FMT>
-__device__ __forceinline__ void split_any(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-  if (FMT == 1) split_pair_f16(v0, v1, hi, lo);
-  else split_pair(v0, v1, hi, lo);
-}
-
-// Scale 2^e that maps a bound B of |values| to at most 2^15 (fp16 max 65504).
-__device__ __forceinline__ int f16_exponent(float bound) {
-  if (!(bound > 0.f) || !isfinite(bound)) return 0;
-  int e = ilogbf(32768.f / bound);
-  return e < -120 ? -120 : (e > 120 ? 120 : e);
-}
-
-__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
-
-__device__ __forceinline__ void st_b16(__nv_bfloat16* p, uint32_t v) {
-  asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"((unsigned short)(v & 0xFFFFu)) : "memory");
-}
-
-// Epilogue of one 32-column chunk held by this thread: TMEM lane = `row`,
-// registers v[0..31] = columns col0 .. col0+31 of the output axis.
-//
-// x pass (PASS 0): row = (j,l) line, the output axis is contiguous in memory,
-//   so each thread writes 16-byte vectors of its own line.
-// y / z passes: row = contiguous index (i, or i + Px*j), the output axis has
-//   a stride, and the 32 lanes of a warp write 32 consecutive elements.
-// sc_in: accumulator -> true value (2^-(e_in + eW), 1 for bf16); sc_out: true
-// value -> stored split value (2^e_out, 1 for bf16); vmax: running max |true|.
-template <int PASS, int MODE, int NP, int FMT>
-__device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col0, int batch, float (&v)[32],
-                                               float sc_in, float sc_out, float& vmax, uint8_t* xstage) {
-  const bool full = col0 + 32 <= a.nout;
-  // Read-modify-write batches: loads of HB elements are issued before their
-  // stores (independent, but the compiler cannot prove it through one
-  // pointer); 16 with 8 epilogue warps, 8 with 16 (the register budget halves).
-  constexpr int HB = epi_warps(MODE) > 8 ? (MODE == OUT_DF_ACCUM ? 4 : 8) : 16;
-  if (FMT == 1) {
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] *= sc_in;
-  }
-  if (PASS == 0) {
-    // Split outputs are stored by the whole warp (staged); the other outputs per lane.
-    if (row >= a.rows && !(MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) return;
-    if (MODE == OUT_DIV_SPLIT) {
-      const int rr = row < a.rows ? row : 0;  // rows past the end (not stored) read valid entries
-      const int j = rr % a.ny, l = rr / a.ny;
-      const float s = __ldg(a.lamy + j) + __ldg(a.lamz + l) + a.c;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int o = col0 + q;
-        const float d = (full || o < a.nout) ? __ldg(a.lamx + o) + s : 1.0f;
-        v[q] = __fdividef(v[q], d);
-      }
-    }
-    if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        if (row < a.rows && (full || col0 + q < a.nout)) vmax = fmaxf(vmax, fabsf(v[q]));
-        v[q] *= sc_out;
-      }
-    }
-    if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
-      double* dst = a.out64 + (size_t)row * a.nx + col0;
-      // Loads first, 16 at a time: the read-modify-writes are independent, but
-      // the compiler cannot prove it through one pointer and would otherwise
-      // serialise one memory round trip per element.
-#pragma unroll
-      for (int h = 0; h < 32; h += HB) {
-        double old[HB];
-#pragma unroll
-        for (int q = 0; q < HB; ++q)
-          old[q] = (MODE == OUT_F64_ACCUM && (full || col0 + h + q < a.nout)) ? dst[h + q] : 0.0;
-#pragma unroll
-        for (int q = 0; q < HB; ++q)
-          if (full || col0 + h + q < a.nout) dst[h + q] = old[q] + f32_to_f64(v[h + q]);
-      }
-    } else {
-      // Each lane holds 32 consecutive outputs of its own row (line).  Written
-      // directly, every 16-byte store of the warp would touch 32 rows; instead
-      // the warp stages its 32 x 32 block in shared memory and writes it back
-      // with 4 lanes per row: each store instruction covers 8 full 64-byte row
-      // segments.  All 32 lanes take part (rows past the end are not stored).
-      const int lane = threadIdx.x & 31;
-      const int row0 = row - lane;
-      uint4 hh[4], ll[4];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        split_any<FMT>(v[8 * g + 0], v[8 * g + 1], hh[g].x, ll[g].x);
-        split_any<FMT>(v[8 * g + 2], v[8 * g + 3], hh[g].y, ll[g].y);
-        split_any<FMT>(v[8 * g + 4], v[8 * g + 5], hh[g].z, ll[g].z);
-        split_any<FMT>(v[8 * g + 6], v[8 * g + 7], hh[g].w, ll[g].w);
-      }
-#pragma unroll
-      for (int part = 0; part < (NP == 3 ? 2 : 1); ++part) {
-        __nv_bfloat16* dst = part == 0 ? a.out_hi : a.out_lo;
-#pragma unroll
-        for (int g = 0; g < 4; ++g)
-          *reinterpret_cast<uint4*>(xstage + lane * XSTAGE_ROW + 16 * g) = part == 0 ? hh[g] : ll[g];
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int r = 8 * k + (lane >> 2), seg = lane & 3;
-          const uint4 val = *reinterpret_cast<const uint4*>(xstage + r * XSTAGE_ROW + 16 * seg);
-          if (row0 + r < a.rows && col0 + 8 * seg + 8 <= a.Px)  // Px is a multiple of 16
-            *reinterpret_cast<uint4*>(dst + (size_t)(row0 + r) * a.Px + col0 + 8 * seg) = val;
-        }
-        __syncwarp();
-      }
-    }
-    return;
-  }
-  if (row >= a.rows) return;
-  int i, j = 0;
-  uint32_t rowoff, cs;
-  if (PASS == 1) {  // row = i, column = j, batch = l
-    i = row;
-    rowoff = (uint32_t)row + (uint32_t)a.Px * (uint32_t)a.ny * (uint32_t)batch;
-    cs = (uint32_t)a.Px;
-  } else {          // row = i + Px*j, column = l
-    i = row % a.Px;
-    j = row / a.Px;
-    rowoff = (uint32_t)row;
-    cs = (uint32_t)a.Px * (uint32_t)a.ny;
-  }
-  if (MODE == OUT_DIV_SPLIT) {
-    const float li = __ldg(a.lamx + (i < a.nx ? i : 0)) + a.c;
-    const float fixed = (PASS == 1) ? __ldg(a.lamz + batch) : __ldg(a.lamy + j);
-    const float* lv = (PASS == 1) ? a.lamy : a.lamz;
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int o = col0 + q;
-      const float d = (full || o < a.nout) ? li + fixed + __ldg(lv + o) : 1.0f;
-      v[q] = __fdividef(v[q], d);
-    }
-  }
-  if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      if (full || col0 + q < a.nout) vmax = fmaxf(vmax, fabsf(v[q]));
-      v[q] *= sc_out;
-    }
-  }
-  if (MODE == OUT_DF_STORE || MODE == OUT_DF_ACCUM || MODE == OUT_DF_ACCUM_F64) {
-    // z pass only: row = i + Px*j is also the index of (i, j, 0) in the
-    // double-FP32 arrays (pitch Px); the FP64 solution has pitch nx.  The
-    // store writes zeros into the pad columns i >= nx (the residual stencil
-    // reads them as the zero boundary values); the updates leave them alone.
-    if (MODE != OUT_DF_STORE && i >= a.nx) return;
-    const size_t dcs = (size_t)a.Px * a.ny;
-    const size_t d0 = (size_t)row + (size_t)col0 * dcs;
-    const size_t cs64 = (size_t)a.nx * a.ny;
-    const size_t o0 = (size_t)i + (size_t)a.nx * j + (size_t)col0 * cs64;
-#pragma unroll
-    for (int h = 0; h < 32; h += HB) {
-      float oh[HB], ol[HB];
-#pragma unroll
-      for (int q = 0; q < HB; ++q) {
-        const bool ok = full || col0 + h + q < a.nout;
-        oh[q] = (MODE != OUT_DF_STORE && ok) ? a.df_hi[d0 + (size_t)(h + q) * dcs] : 0.f;
-        ol[q] = (MODE != OUT_DF_STORE && ok) ? a.df_lo[d0 + (size_t)(h + q) * dcs] : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < HB; ++q) {
-        if (!(full || col0 + h + q < a.nout)) continue;
-        const size_t d = d0 + (size_t)(h + q) * dcs;
-        if (MODE == OUT_DF_STORE) {
-          a.df_hi[d] = i < a.nx ? v[h + q] : 0.f;
-          a.df_lo[d] = 0.f;
-        } else {
-          // (oh + ol) + v: two-sum of the leading parts, then renormalise.
-          const float sum = oh[q] + v[h + q];
-          const float bb = sum - oh[q];
-          const float err = (oh[q] - (sum - bb)) + (v[h + q] - bb);
-          const float t = ol[q] + err;
-          const float nh = sum + t;
-          const float nl = t - (nh - sum);
-          if (MODE == OUT_DF_ACCUM) {
-            a.df_hi[d] = nh;
-            a.df_lo[d] = nl;
-          } else {
-            a.out64[o0 + (size_t)(h + q) * cs64] = f32_to_f64(nh) + f32_to_f64(nl);
-          }
-        }
-      }
-    }
-  } else if (MODE == OUT_F64 || MODE == OUT_F64_ACCUM) {
-    if (i >= a.nx) return;
-    size_t base, cs64;
-    if (PASS == 1) { base = (size_t)i + (size_t)a.nx * a.ny * batch; cs64 = (size_t)a.nx; }
-    else { base = (size_t)i + (size_t)a.nx * j; cs64 = (size_t)a.nx * a.ny; }
-    double* p = a.out64 + base + (size_t)col0 * cs64;
-    // Loads first, 16 at a time (see the x pass).
-#pragma unroll
-    for (int h = 0; h < 32; h += HB) {
-      double old[HB];
-#pragma unroll
-      for (int q = 0; q < HB; ++q)
-        old[q] = (MODE == OUT_F64_ACCUM && (full || col0 + h + q < a.nout)) ? p[(size_t)(h + q) * cs64] : 0.0;
-#pragma unroll
-      for (int q = 0; q < HB; ++q)
-        if (full || col0 + h + q < a.nout) p[(size_t)(h + q) * cs64] = old[q] + f32_to_f64(v[h + q]);
-    }
-  } else {
-    __nv_bfloat16* ph = a.out_hi + rowoff + (size_t)col0 * cs;
-    __nv_bfloat16* pl = a.out_lo + rowoff + (size_t)col0 * cs;
-#pragma unroll
-    for (int q = 0; q < 32; q += 2) {
-      uint32_t hh, ll;
-      split_any<FMT>(v[q], v[q + 1], hh, ll);
-      if (full || col0 + q < a.nout) { st_b16(ph, hh); if (NP == 3) st_b16(pl, ll); }
-      ph += cs; pl += cs;
-      if (full || col0 + q + 1 < a.nout) { st_b16(ph, hh >> 16); if (NP == 3) st_b16(pl, ll >> 16); }
-      ph += cs; pl += cs;
-    }
-  }
-}
+using namespace tcx;
 
 // Thread-block clusters of CL CTAs (CL = 1, 2 or 4) work on CL consecutive M
 // tiles that share one N tile, so they need the same W tile: each CTA loads
@@ -621,6 +319,8 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
 
 }  // namespace
 
+using namespace tcx;
+
 namespace {
 
 // Cluster size of the W multicast (1 = none).
@@ -732,7 +432,37 @@ static constexpr CUtensorMapSwizzle SWZ_MN = CU_TENSOR_MAP_SWIZZLE_128B;
 // Launches that still have to run with the producer stalled (sem3d_inject_stall).
 std::atomic<int> g_stall_launches{0};
 
+// Kernel variant per pass shape (process-wide): TC_SINGLE = one CTA per
+// 128 x 256 tile, W multicast in clusters of 4, 4 stages; TC_PAIR = one
+// cta_group::2 MMA per pair of SMs on 256 x 256 tiles, 6 stages.  Chosen by
+// tc_autotune (measured) or pinned by tc_set_config; unmeasured shapes use
+// TC_SINGLE.
+std::mutex g_tc_cfg_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tc_cfg;
+
+std::tuple<int, int, int, int, int> tc_key(int axis, const Geom& g, int nprod) {
+  return std::make_tuple(axis, g.nx, g.ny, g.nz, nprod);
+}
+
+int tc_config(int axis, const Geom& g, int nprod) {
+  std::lock_guard<std::mutex> lk(g_tc_cfg_mu);
+  auto it = g_tc_cfg.find(tc_key(axis, g, nprod));
+  return it == g_tc_cfg.end() ? TC_SINGLE : it->second;
+}
+
+bool tc_config_known(int axis, const Geom& g, int nprod) {
+  std::lock_guard<std::mutex> lk(g_tc_cfg_mu);
+  return g_tc_cfg.count(tc_key(axis, g, nprod)) != 0;
+}
+
+void tc_set_config(int axis, const Geom& g, int nprod, int cfg) {
+  std::lock_guard<std::mutex> lk(g_tc_cfg_mu);
+  g_tc_cfg[tc_key(axis, g, nprod)] = cfg;
+}
+
 void tc_inject_stall(int launches) { g_stall_launches.store(launches); }
+
+int tc_swap_stall(int launches) { return g_stall_launches.exchange(launches); }
 
 int tc_take_stall() {
   int left = g_stall_launches.load();
@@ -741,13 +471,14 @@ int tc_take_stall() {
   return left > 0 ? 1 : 0;
 }
 
-cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
-                                       TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
-                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
-                                       DfBuffers df, int nprod, const F16Pass* f16) {
+namespace tcx {
+
+cudaError_t prepare_pass(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in, TcBuffers out,
+                         double* out64, int epi, const float* lamx, const float* lamy, const float* lamz, int* err_flag,
+                         DfBuffers df, int nprod, const F16Pass* f16, bool pair, PassSetup& ps) {
   if (nprod != 1 && nprod != 3) return cudaErrorInvalidValue;
   const int fmt = f16 ? 1 : 0;
-  if (fmt == 1 && nprod != 3) return cudaErrorInvalidValue;
+  if (fmt == 1 && (nprod != 3 || pair)) return cudaErrorInvalidValue;
   int mode;
   if (epi == EPI_DF_STORE || epi == EPI_DF_ACCUM || epi == EPI_DF_ACCUM_F64) {
     if (axis != 2 || !df.hi || !df.lo || (epi == EPI_DF_ACCUM_F64 && !out64)) return cudaErrorInvalidValue;
@@ -758,8 +489,9 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
     mode = (epi == EPI_DIV) ? OUT_DIV_SPLIT : OUT_SPLIT;
   }
   if (out64 && epi == EPI_DIV) return cudaErrorInvalidValue;
-  TcArgs a{};
-  a.stall = tc_take_stall();
+  TcArgs& a = ps.a;
+  a = TcArgs{};
+  ps.mode = mode;
   a.df_hi = df.hi;
   a.df_lo = df.lo;
   if (f16) {
@@ -774,7 +506,6 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   a.out_hi = out.hi; a.out_lo = out.lo; a.out64 = out64;
   a.lamx = lamx; a.lamy = lamy; a.lamz = lamz; a.c = (float)g.c;
   a.err = err_flag;
-  CUtensorMap mAh, mAl, mBh, mBl;
   const uint64_t Px = (uint64_t)g.Px, ny = (uint64_t)g.ny, nz = (uint64_t)g.nz;
   bool ok = true;
   int nin = 0;
@@ -783,31 +514,34 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
     const uint64_t dims[2] = {(uint64_t)g.nx, ny * nz};
     const uint64_t str[1] = {Px * 2};
     const uint32_t box[2] = {BK, 128};
-    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box, SWZ_K) && make_map(&mAl, in.lo, 2, dims, str, box, SWZ_K);
+    ok = ok && make_map(&ps.mAh, in.hi, 2, dims, str, box, SWZ_K) && make_map(&ps.mAl, in.lo, 2, dims, str, box, SWZ_K);
     a.rows = g.ny * g.nz; a.batches = 1; nin = g.nx;
   } else if (axis == 1) {
     // A: dims {i: Px, j: ny, l: nz}; box {64 rows, BK K, 1}
     const uint64_t dims[3] = {Px, ny, nz};
     const uint64_t str[2] = {Px * 2, Px * ny * 2};
     const uint32_t box[3] = {64, BK, 1};
-    ok = ok && make_map(&mAh, in.hi, 3, dims, str, box, SWZ_MN) && make_map(&mAl, in.lo, 3, dims, str, box, SWZ_MN);
+    ok = ok && make_map(&ps.mAh, in.hi, 3, dims, str, box, SWZ_MN) &&
+         make_map(&ps.mAl, in.lo, 3, dims, str, box, SWZ_MN);
     a.rows = g.Px; a.batches = g.nz; nin = g.ny;
   } else {
     // A: dims {m = i + Px*j: Px*ny, l: nz}; box {64 rows, BK K}
     const uint64_t dims[2] = {Px * ny, nz};
     const uint64_t str[1] = {Px * ny * 2};
     const uint32_t box[2] = {64, BK};
-    ok = ok && make_map(&mAh, in.hi, 2, dims, str, box, SWZ_MN) && make_map(&mAl, in.lo, 2, dims, str, box, SWZ_MN);
+    ok = ok && make_map(&ps.mAh, in.hi, 2, dims, str, box, SWZ_MN) &&
+         make_map(&ps.mAl, in.lo, 2, dims, str, box, SWZ_MN);
     a.rows = g.Px * g.ny; a.batches = 1; nin = g.nz;
   }
   {
     // W: dims {t: n, o: n}, row pitch Kp*2 B; box {BK (K), BN/CLUSTER rows}
+    // (pair kernel: BN/2 rows, each CTA of the pair stages half of the tile)
     const uint64_t dims[2] = {(uint64_t)W.n, (uint64_t)W.n};
     const uint64_t str[1] = {(uint64_t)W.Kp * 2};
-    const uint32_t box[2] = {BK, (uint32_t)(BN / CLUSTER)};
+    const uint32_t box[2] = {BK, (uint32_t)(pair ? BN / 2 : BN / CLUSTER)};
     const void* wh = fmt ? (const void*)W.W16_hi[which] : (const void*)W.W_hi[which];
     const void* wl = fmt ? (const void*)W.W16_lo[which] : (const void*)W.W_lo[which];
-    ok = ok && make_map(&mBh, wh, 2, dims, str, box, SWZ_K) && make_map(&mBl, wl, 2, dims, str, box, SWZ_K);
+    ok = ok && make_map(&ps.mBh, wh, 2, dims, str, box, SWZ_K) && make_map(&ps.mBl, wl, 2, dims, str, box, SWZ_K);
   }
   if (!ok) return cudaErrorInvalidValue;
   a.nout = W.n;
@@ -815,11 +549,98 @@ cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W
   a.n_tiles = (W.n + BN - 1) / BN;
   a.k_blocks = (nin + BK - 1) / BK;
   a.kc = (fmt == 1 && SEM3D_TC_CHUNK_KBLOCKS > 0) ? SEM3D_TC_CHUNK_KBLOCKS : a.k_blocks;
+  return cudaSuccess;
+}
+
+}  // namespace tcx
+
+cudaError_t launch_mode_product_bf16x3(const Geom& g, int axis, const DevAxis& W, int which, TcBuffers in,
+                                       TcBuffers out, double* out64, int epi, const float* lamx, const float* lamy,
+                                       const float* lamz, int* err_flag, int num_sms, cudaStream_t s,
+                                       DfBuffers df, int nprod, const F16Pass* f16) {
+  const int fmt = f16 ? 1 : 0;
+  const bool pair = fmt == 0 && tc_config(axis, g, nprod) == TC_PAIR;
+  PassSetup ps;
+  cudaError_t e = prepare_pass(g, axis, W, which, in, out, out64, epi, lamx, lamy, lamz, err_flag, df, nprod, f16,
+                               pair, ps);
+  if (e != cudaSuccess) return e;
+  TcArgs& a = ps.a;
+  a.stall = tc_take_stall();
+  if (pair) {
+    const long long work = (long long)((a.m_tiles + 1) / 2) * a.n_tiles * a.batches;
+    if (work >= (1LL << 31)) return cudaErrorInvalidValue;
+    return launch_pair_pass(axis, nprod, ps, work, num_sms, s);
+  }
   const long long work = (long long)((a.m_tiles + CLUSTER - 1) / CLUSTER) * a.n_tiles * a.batches;
   if (work >= (1LL << 31)) return cudaErrorInvalidValue;
-  if (axis == 0) return launch_tc_mode<0>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);
-  if (axis == 1) return launch_tc_mode<1>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);
-  return launch_tc_mode<2>(mode, nprod, fmt, mAh, mAl, mBh, mBl, a, work, num_sms, s);
+  const int mode = ps.mode;
+  if (axis == 0) return launch_tc_mode<0>(mode, nprod, fmt, ps.mAh, ps.mAl, ps.mBh, ps.mBl, a, work, num_sms, s);
+  if (axis == 1) return launch_tc_mode<1>(mode, nprod, fmt, ps.mAh, ps.mAl, ps.mBh, ps.mBl, a, work, num_sms, s);
+  return launch_tc_mode<2>(mode, nprod, fmt, ps.mAh, ps.mAl, ps.mBh, ps.mBl, a, work, num_sms, s);
+}
+
+// Measure both kernel variants on each pass shape of g not measured before.
+// The synthetic pass keeps the contracted extent, the output extent and the
+// access pattern of the real one and truncates the grid so that a split array
+// holds at most 2^26 elements (nz for the x and y passes, ny for the z pass);
+// inputs are zeros.  One warm-up and three timed launches per variant (CUDA
+// events on a private stream); the faster variant is recorded for g.
+cudaError_t tc_autotune(const Geom& g, const DevAxis* ax, int nprod, int* err_flag, int num_sms) {
+  bool need = false;
+  for (int axis = 0; axis < 3; ++axis) need = need || !tc_config_known(axis, g, nprod);
+  if (!need) return cudaSuccess;
+  constexpr size_t kCap = size_t(1) << 26;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  __nv_bfloat16* buf = nullptr;
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreate(&ev[q]);
+  const size_t plane = (size_t)g.Px * g.ny;
+  size_t elems = 0;
+  Geom gs[3];
+  for (int axis = 0; axis < 3; ++axis) {
+    gs[axis] = g;
+    if (axis < 2) {
+      gs[axis].nz = (int)std::min<size_t>(g.nz, std::max<size_t>(1, kCap / plane));
+    } else {
+      gs[axis].ny = (int)std::min<size_t>(g.ny, std::max<size_t>(1, kCap / ((size_t)g.Px * g.nz)));
+    }
+    elems = std::max(elems, (size_t)gs[axis].Px * gs[axis].ny * gs[axis].nz);
+  }
+  const size_t bytes = (elems * sizeof(__nv_bfloat16) + 255) & ~size_t(255);
+  const int stalls = g_stall_launches.exchange(0);  // measurement launches take no injected stall
+  if (e == cudaSuccess) e = cudaMalloc(&buf, 4 * bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 4 * bytes, s);
+  for (int axis = 0; axis < 3 && e == cudaSuccess; ++axis) {
+    if (tc_config_known(axis, g, nprod)) continue;
+    uint8_t* b8 = reinterpret_cast<uint8_t*>(buf);
+    TcBuffers in{reinterpret_cast<__nv_bfloat16*>(b8), reinterpret_cast<__nv_bfloat16*>(b8 + bytes)};
+    TcBuffers out{reinterpret_cast<__nv_bfloat16*>(b8 + 2 * bytes), reinterpret_cast<__nv_bfloat16*>(b8 + 3 * bytes)};
+    float best_ms = 0.f;
+    int best = TC_SINGLE;
+    for (int variant : {TC_SINGLE, TC_PAIR}) {
+      tc_set_config(axis, gs[axis], nprod, variant);
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess)
+          e = launch_mode_product_bf16x3(gs[axis], axis, ax[axis], 0, in, out, nullptr, EPI_STORE, nullptr, nullptr,
+                                         nullptr, err_flag, num_sms, s, DfBuffers{nullptr, nullptr}, nprod);
+      }
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e == cudaSuccess && (variant == TC_SINGLE || ms < best_ms)) { best_ms = ms; best = variant; }
+    }
+    if (e == cudaSuccess) tc_set_config(axis, g, nprod, best);
+  }
+  if (buf) cudaFree(buf);
+  for (int q = 0; q < 2; ++q)
+    if (ev[q]) cudaEventDestroy(ev[q]);
+  cudaStreamDestroy(s);
+  g_stall_launches.store(stalls);
+  return e;
 }
 
 }  // namespace sem3d

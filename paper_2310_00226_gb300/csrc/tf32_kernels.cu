@@ -26,6 +26,11 @@
 #include "sem3d_internal.h"
 #include "tc_ptx.cuh"
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace sem3d {
 
 namespace {
@@ -255,6 +260,166 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
   }
 }
 
+// ---------------------------------------------------------------- CTA-pair kernel
+//
+// The same pass with one kind::tf32 MMA per pair of SMs (cta_group::2, M =
+// 256): CTA r of a cluster of 2 stages rows [128 r, 128 r + 128) of the A tile
+// and of the W tile, 32 KB per stage, 6 stages (the one-CTA kernel holds 4 of
+// 48 KB).  The protocol is that of the split-bf16 pair kernel: both CTAs' TMA
+// loads complete on the leader's full barrier, which the leader arms with the
+// pair's bytes; the leader's MMA commits arrive on both CTAs' empty / tfull
+// barriers (multicast); both CTAs' epilogue warps release an accumulator on
+// the leader's tempty barrier; every wait is bounded.
+constexpr int TP_STAGES = 6;
+constexpr int TP_B_BYTES = (T_BN / 2) * T_BK * 4;    // 16 KB: this CTA's half of W
+constexpr int TP_STAGE_BYTES = T_A_BYTES + TP_B_BYTES;  // 32 KB
+constexpr int TP_SMEM = TP_STAGES * TP_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+__device__ __forceinline__ void mma_tf32_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(t_threads(MODE), 1)
+    mode_product_tf32_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                                  const Tf32Args a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TP_STAGES * TP_STAGE_BYTES);
+  // bars: full[TP_STAGES], empty[TP_STAGES], tfull[2], tempty[2], drain[1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TP_STAGES + 5);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (TP_STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * TP_STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * TP_STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * TP_STAGES + 4);
+  constexpr uint16_t kPair = 3;
+  constexpr int ROWS_B = T_BN / 2;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster_ctarank();
+  const int pid = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TP_STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(tfull_bar(b), 1); mbar_init(tempty_bar(b), 2 * t_epi_warps(MODE)); }
+    mbar_init(drain_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(T_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers are initialised before any cross-CTA signal
+  tc_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+
+  // Pair tile pt -> (M pair mp, N tile nt); this CTA's M tile is 2 mp + rank.
+  const int m_pairs = (a.m_tiles + 1) / 2;
+  const int total_pt = m_pairs * a.n_tiles;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer (each CTA)
+    const uint32_t full_leader0 = mapa_shared(full_bar(0), 0);
+    int it = 0;
+    bool ok = true;
+    for (int pt = pid; pt < total_pt && ok && !a.stall; pt += npairs) {
+      const int mp = pt / a.n_tiles, nt = pt - mp * a.n_tiles;
+      const int m0 = (2 * mp + rank) * T_BM, n0 = nt * T_BN + rank * ROWS_B;
+      for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
+        const int s = it % TP_STAGES;
+        if (!mbar_wait(empty_bar(s), ((it / TP_STAGES) & 1) ^ 1, a.err)) { ok = false; break; }
+        const uint32_t st = smem_u32(smem + s * TP_STAGE_BYTES);
+        const uint32_t fb = full_leader0 + 8u * s;
+        if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * TP_STAGE_BYTES);
+        const int k0 = kb * T_BK;
+        tma_load_2d_pair(st, &tmA, fb, k0, m0);
+        tma_load_2d_pair(st + T_A_BYTES, &tmB, fb, k0, n0);
+      }
+    }
+    // Drain (see the split-bf16 pair kernel): the last fill of each stage has
+    // landed and its MMAs have completed before this CTA may exit.
+    const int armed = it;
+    for (int q = (armed > TP_STAGES ? armed - TP_STAGES : 0); q < armed; ++q) {
+      if (rank == 0) mbar_wait(full_bar(q % TP_STAGES), (q / TP_STAGES) & 1, nullptr);
+      mbar_wait(empty_bar(q % TP_STAGES), (q / TP_STAGES) & 1, nullptr);
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------ MMA issuer (leader only)
+    constexpr uint32_t idesc = make_idesc_tf32(2 * T_BM, T_BN);
+    int it = 0, cc = 0;
+    bool ok = true;
+    for (int pt = pid; pt < total_pt && ok; pt += npairs, ++cc) {
+      const int buf = cc & 1;
+      if (!mbar_wait_cluster(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err)) break;
+      tc_fence_after();
+      const uint32_t tmem_d = tmem_base + (uint32_t)(buf * T_BN);
+      for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
+        const int s = it % TP_STAGES;
+        if (!mbar_wait(full_bar(s), (it / TP_STAGES) & 1, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * TP_STAGE_BYTES);
+#pragma unroll
+        for (int k8 = 0; k8 < T_BK / 8; ++k8) {
+          const uint64_t da = smem_desc(st + k8 * 32u, 16u, 1024u, LAYOUT_SW128);
+          const uint64_t db = smem_desc(st + T_A_BYTES + k8 * 32u, 16u, 1024u, LAYOUT_SW128);
+          mma_tf32_pair(tmem_d, da, db, idesc, (kb | k8) ? 1u : 0u);
+        }
+        mma_commit_pair_mc(empty_bar(s), kPair);
+      }
+      if (!ok) break;
+      mma_commit_pair_mc(tfull_bar(buf), kPair);
+    }
+    mma_commit_pair_mc(drain_bar, 1);
+    mbar_wait(drain_bar, 0, nullptr);
+  } else if (warp >= 2) {
+    // ------------------------------------------------ epilogue (each CTA, its own 128 rows)
+    const int quad = warp & 3;
+    const int slice = (warp - 2) >> 2;
+    constexpr int COLS = T_BN / (t_epi_warps(MODE) / 4);
+    const uint32_t tempty_leader0 = mapa_shared(tempty_bar(0), 0);
+    int cc = 0;
+    for (int pt = pid; pt < total_pt; pt += npairs, ++cc) {
+      const int mp = pt / a.n_tiles, nt = pt - mp * a.n_tiles;
+      const int mt = 2 * mp + rank;
+      const int buf = cc & 1;
+      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err)) break;
+      tc_fence_after();
+      const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * T_BN + slice * COLS);
+      const int row = mt * T_BM + quad * 32 + lane;
+#pragma unroll 1
+      for (int ch = 0; ch < COLS / 32; ++ch) {
+        const int col0 = nt * T_BN + slice * COLS + ch * 32;
+        if (col0 >= a.nout || mt >= a.m_tiles) break;  // warp-uniform
+        float v[32];
+        tmem_ld32(lane_addr + (uint32_t)(ch * 32), v);
+        tf32_epilogue<MODE>(a, row, col0, v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(tempty_leader0 + 8u * buf);
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(T_TMEM_COLS));
+  }
+}
+
 // FP64 array (x fastest, pitch nx) -> TF32-rounded FP32 array at pitch Px.
 // Blocks walk the (j, l) lines; a lane converts 4 consecutive entries and
 // writes them as one 16-byte store (rows of pitch Px, a multiple of 16, are
@@ -308,7 +473,61 @@ cudaError_t launch_tf32(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32
   return cudaLaunchKernelEx(&cfg, kern, mA, mB, a);
 }
 
+template <int MODE>
+cudaError_t launch_tf32_pair(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32Args& a, long long work_pairs,
+                             int num_sms, cudaStream_t s) {
+  auto kern = mode_product_tf32_pair_kernel<MODE>;
+  static int max_pairs = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(t_threads(MODE));
+  cfg.dynamicSmemBytes = TP_SMEM;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (max_pairs == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(2 * (num_sms / 2));
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_pairs = n;
+  }
+  const long long pairs = work_pairs < max_pairs ? work_pairs : max_pairs;
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  cfg.stream = s;
+  return cudaLaunchKernelEx(&cfg, kern, mA, mB, a);
+}
+
+// Kernel variant per TF32 pass shape (nK, d1, d2), process-wide: TC_SINGLE
+// (one CTA per tile, W multicast in clusters of 4) or TC_PAIR.
+std::mutex g_tf32_cfg_mu;
+std::map<std::tuple<int, int, int>, int> g_tf32_cfg;
+
+int tf32_variant(int nK, int d1, int d2) {
+  std::lock_guard<std::mutex> lk(g_tf32_cfg_mu);
+  auto it = g_tf32_cfg.find(std::make_tuple(nK, d1, d2));
+  return it == g_tf32_cfg.end() ? TC_SINGLE : it->second;
+}
+
 }  // namespace
+
+bool tf32_config_known(int nK, int d1, int d2) {
+  std::lock_guard<std::mutex> lk(g_tf32_cfg_mu);
+  return g_tf32_cfg.count(std::make_tuple(nK, d1, d2)) != 0;
+}
+
+void tf32_set_config(int nK, int d1, int d2, int cfg) {
+  std::lock_guard<std::mutex> lk(g_tf32_cfg_mu);
+  g_tf32_cfg[std::make_tuple(nK, d1, d2)] = cfg;
+}
+
+int tf32_config(int nK, int d1, int d2) { return tf32_variant(nK, d1, d2); }
 
 cudaError_t launch_to_tf32(const Geom& g, const double* in, float* out, cudaStream_t s) {
   const long long lines = (long long)g.ny * g.nz;
@@ -358,13 +577,25 @@ cudaError_t launch_mode_product_tf32(const Tf32Pass& p, int* err_flag, int num_s
     if (!make_map(&mA, p.in, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_DATA_TYPE_FLOAT32))
       return cudaErrorInvalidValue;
   }
+  const bool pair = tf32_variant(p.nK, p.d1, p.d2) == TC_PAIR;
   {
     // W: dims {t: nK, o: nK}, row stride Wpitch*4 B; box {T_BK, T_BN / T_CL}
+    // (pair kernel: T_BN / 2 rows, each CTA of the pair stages half of the tile)
     const uint64_t dims[2] = {(uint64_t)p.nK, (uint64_t)p.nK};
     const uint64_t str[1] = {(uint64_t)p.Wpitch * 4};
-    const uint32_t box[2] = {T_BK, (uint32_t)(T_BN / T_CL)};
+    const uint32_t box[2] = {T_BK, (uint32_t)(pair ? T_BN / 2 : T_BN / T_CL)};
     if (!make_map(&mB, p.W, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_DATA_TYPE_FLOAT32))
       return cudaErrorInvalidValue;
+  }
+  if (pair) {
+    const long long work = (long long)((a.m_tiles + 1) / 2) * a.n_tiles;
+    if (work >= (1LL << 31)) return cudaErrorInvalidValue;
+    switch (mode) {
+      case T_OUT_T32: return launch_tf32_pair<T_OUT_T32>(mA, mB, a, work, num_sms, s);
+      case T_OUT_T32_DIV: return launch_tf32_pair<T_OUT_T32_DIV>(mA, mB, a, work, num_sms, s);
+      case T_OUT_F64: return launch_tf32_pair<T_OUT_F64>(mA, mB, a, work, num_sms, s);
+      default: return launch_tf32_pair<T_OUT_F64_ACCUM>(mA, mB, a, work, num_sms, s);
+    }
   }
   const long long work = (long long)((a.m_tiles + T_CL - 1) / T_CL) * a.n_tiles;
   if (work >= (1LL << 31)) return cudaErrorInvalidValue;
@@ -374,6 +605,72 @@ cudaError_t launch_mode_product_tf32(const Tf32Pass& p, int* err_flag, int num_s
     case T_OUT_F64: return launch_tf32<T_OUT_F64>(mA, mB, a, work, num_sms, s);
     default: return launch_tf32<T_OUT_F64_ACCUM>(mA, mB, a, work, num_sms, s);
   }
+}
+
+// Measure both kernel variants on the three TF32 pass shapes of g (along x,
+// y and z: nK = that axis, rows = the other two) that the process has not
+// measured: a synthetic pass with the real nK, d1 and output layout and d2
+// truncated so that an array holds at most 2^26 elements; inputs are zeros;
+// one warm-up and three timed launches per variant.
+cudaError_t tf32_autotune(const Geom& g, const DevAxis* ax, int* err_flag, int num_sms) {
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  bool need = false;
+  for (int a = 0; a < 3; ++a) need = need || !tf32_config_known(n3[a], n3[(a + 1) % 3], n3[(a + 2) % 3]);
+  if (!need) return cudaSuccess;
+  constexpr size_t kCap = size_t(1) << 26;
+  Tf32Pass ps[3];
+  size_t in_elems = 0, out_elems = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    Tf32Pass& t = ps[a];
+    t.nK = n3[a]; t.d1 = n3[a1]; t.P0 = pad16(n3[a]); t.P1 = pad16(n3[a1]);
+    const size_t per = (size_t)t.P0 * t.d1 > (size_t)t.P1 * t.nK ? (size_t)t.P0 * t.d1 : (size_t)t.P1 * t.nK;
+    t.d2 = (int)std::min<size_t>(n3[a2], std::max<size_t>(1, kCap / per));
+    in_elems = std::max(in_elems, (size_t)t.P0 * t.d1 * t.d2);
+    out_elems = std::max(out_elems, (size_t)t.P1 * t.d2 * t.nK);
+    t.W = ax[a].Wt32[0];
+    t.Wpitch = ax[a].Kp;
+    t.epi = EPI_STORE;
+  }
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreate(&ev[q]);
+  float* buf = nullptr;
+  const size_t in_bytes = (in_elems * sizeof(float) + 255) & ~size_t(255);
+  const size_t out_bytes = (out_elems * sizeof(float) + 255) & ~size_t(255);
+  const int stalls = tc_swap_stall(0);  // measurement launches take no injected stall
+  if (e == cudaSuccess) e = cudaMalloc(&buf, in_bytes + out_bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, in_bytes + out_bytes, s);
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+    Tf32Pass t = ps[a];
+    const int d2 = n3[(a + 2) % 3];
+    if (tf32_config_known(t.nK, t.d1, d2)) continue;
+    t.in = buf;
+    t.out32 = reinterpret_cast<float*>(reinterpret_cast<char*>(buf) + in_bytes);
+    float best_ms = 0.f;
+    int best = TC_SINGLE;
+    for (int variant : {TC_SINGLE, TC_PAIR}) {
+      tf32_set_config(t.nK, t.d1, t.d2, variant);
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess) e = launch_mode_product_tf32(t, err_flag, num_sms, s);
+      }
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e == cudaSuccess && (variant == TC_SINGLE || ms < best_ms)) { best_ms = ms; best = variant; }
+    }
+    if (e == cudaSuccess) tf32_set_config(t.nK, t.d1, d2, best);
+  }
+  if (buf) cudaFree(buf);
+  for (int q = 0; q < 2; ++q)
+    if (ev[q]) cudaEventDestroy(ev[q]);
+  cudaStreamDestroy(s);
+  tc_swap_stall(stalls);
+  return e;
 }
 
 }  // namespace sem3d

@@ -47,6 +47,8 @@ EXPORTS = (
     "sem3d_launch_count",
     "sem3d_tuned_config",
     "sem3d_set_tuned_config",
+    "sem3d_tc_config",
+    "sem3d_set_tc_config",
     "sem3d_inject_stall",
     "sem3d_solve_fp64_static",
     "sem3d_destroy",
@@ -100,6 +102,8 @@ def lib() -> ctypes.CDLL:
     L.sem3d_launch_count.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]
     L.sem3d_tuned_config.argtypes = [c_void_p, c_int, ctypes.POINTER(c_int)]
     L.sem3d_set_tuned_config.argtypes = [c_void_p, c_int, c_int]
+    L.sem3d_tc_config.argtypes = [c_void_p, c_int, ctypes.POINTER(c_int)]
+    L.sem3d_set_tc_config.argtypes = [c_void_p, c_int, c_int]
     L.sem3d_inject_stall.argtypes = [c_void_p, c_int]
     L.sem3d_solve_fp64_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.sem3d_destroy.argtypes = [c_void_p]
@@ -271,6 +275,16 @@ class Plan:
     def set_tuned_config(self, axis: int, config: int):
         """Pin an FP32 kernel configuration for this plan's pass shape along axis."""
         _check(lib().sem3d_set_tuned_config(self._h, axis, config), "sem3d_set_tuned_config")
+
+    def tc_config(self, axis: int) -> int:
+        """Tensor-core kernel (0 = single CTA, 1 = CTA pair) chosen for the pass along axis."""
+        c = ctypes.c_int()
+        _check(lib().sem3d_tc_config(self._h, axis, ctypes.byref(c)), "sem3d_tc_config")
+        return c.value
+
+    def set_tc_config(self, axis: int, config: int):
+        """Pin the tensor-core kernel (0 = single CTA, 1 = CTA pair) for this plan's pass shape along axis."""
+        _check(lib().sem3d_set_tc_config(self._h, axis, config), "sem3d_set_tc_config")
 
     def nodes(self, axis: int) -> np.ndarray:
         x = np.empty(self.n[axis])

@@ -1,8 +1,13 @@
 """GPU parity of sem3d_solve_batched against the oracle, problem by problem.
 
-Grouped path: every plan SEM3D_FP32 with the same sweeps (one launch per
-pass for all problems).  Stream path: mixed tiers.  Tolerance: relative L-inf
-1e-12 after refinement (2 sweeps FP32, 3 sweeps BF16x3, 1 sweep FP64).
+Grouped paths: every plan SEM3D_FP32 with the same sweeps (one FP32 launch
+per pass for all problems), or every plan in one split tier (BF16x3 / BF16)
+with the same sweeps and residual schedule (one persistent CTA-pair tcgen05
+launch per pass for all problems, per-problem tensor maps in a device table).
+Stream path: mixed tiers.  Tolerance: relative L-inf 1e-12 after refinement
+(2 sweeps FP32, 3 sweeps BF16x3, 1 sweep FP64).  The grouped tensor-core
+path issues the same MMAs as a plan's own solve, so its results must be
+bit-identical to sem3d_solve of each plan.
 """
 
 import numpy as np
@@ -39,7 +44,8 @@ def _refs(probs):
     return refs
 
 
-@pytest.mark.parametrize("mode", ["grouped_fp32", "grouped_fp32_mixed_tiles", "streams_mixed"])
+@pytest.mark.parametrize("mode", ["grouped_fp32", "grouped_fp32_mixed_tiles", "streams_mixed",
+                                  "grouped_bf16x3_mixed", "grouped_bf16x3_fp64", "grouped_bf16x3_df"])
 def test_batched_matches_oracle(sem3d, mode):
     probs = _problems()
     refs = _refs(probs)
@@ -53,6 +59,9 @@ def test_batched_matches_oracle(sem3d, mode):
                     # one grouped launch runs problems with different tile shapes
                     for a in range(3):
                         p.set_tuned_config(a, (q + a) % 6)
+            elif mode.startswith("grouped_bf16x3"):
+                p.set_precision("bf16x3", 3)
+                p.set_residual(mode.split("_")[-1])
             else:
                 p.set_precision(*[("fp32", 2), ("bf16x3", 3), ("fp64", 1), ("tf32", 5)][q % 4])
             plans.append(p)
@@ -76,3 +85,34 @@ def test_batched_rejects_duplicate_plans(sem3d):
         u = torch.empty_like(f)
         with pytest.raises(sem3d.Sem3dError):
             sem3d.solve_batched([p, p], [f, f], [u, u])
+
+
+@pytest.mark.parametrize("tier,sweeps,residual", [("bf16x3", 3, "mixed"), ("bf16x3", 2, "fp64"), ("bf16x3", 2, "df"),
+                                                  ("bf16", 0, "mixed"), ("bf16", 2, "mixed")])
+def test_grouped_tensor_core_batch_is_bit_identical_to_single_solves(sem3d, tier, sweeps, residual):
+    # Problems large enough for several pair tiles, N tiles and K blocks each,
+    # of uneven n and k; the grouped launches must reproduce each plan's solve.
+    probs = batched_helmholtz(count=6, seed=5, sizes=(63, 127, 191, 255), degrees=(2, 4))
+    plans, fs, us, ref = [], [], [], []
+    try:
+        for pr in probs:
+            p = sem3d.Plan(*pr["n3"], pr["k"], (1.0, 1.0, 1.0), pr["c"])
+            p.set_precision(tier, sweeps)
+            p.set_residual(residual)
+            f = torch.from_numpy(random_rhs(*pr["n3"], seed=pr["seed"])).cuda()
+            u = torch.empty_like(f)
+            p.solve(f, u)
+            p.sync_check()
+            plans.append(p)
+            fs.append(f)
+            ref.append(u.cpu().numpy())
+            us.append(torch.full_like(f, float("nan")))
+        for _ in range(2):
+            sem3d.solve_batched(plans, fs, us)
+            plans[0].sync_check()
+            for q in range(len(probs)):
+                got = us[q].cpu().numpy()
+                assert np.array_equal(got, ref[q]), (tier, q, probs[q], float(np.abs(got - ref[q]).max()))
+    finally:
+        for p in plans:
+            p.close()
