@@ -559,6 +559,10 @@ def _timed_host(fn, steps, warmup, torch):
     return (time.perf_counter() - t0) * 1e3 / steps
 
 
+def _progress(msg: str):
+    print(f"bench.py [{time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_workload(args, rank: int):
     """Batched Helmholtz, Cahn-Hilliard and Schroedinger-PCG workloads (one JSON
     line each; not the headline metric)."""
@@ -578,33 +582,28 @@ def run_workload(args, rank: int):
             fs.append(torch.from_numpy(random_rhs(nx, ny, nz, pr["seed"])).cuda())
             us.append(torch.empty_like(fs[-1]))
         dofs = sum(p.numel for p in plans)
+        _progress(f"batched: {len(plans)} plans, {dofs} DoF")
         res = {}
         for prec, sweeps in (("fp32", 2), ("bf16x3", 3)):
             for p in plans:
                 p.set_precision(prec, sweeps)
+            _progress(f"batched: {prec} set_precision done")
             ms = _timed_host(lambda: sem3d.solve_batched(plans, fs, us, stream), args.steps, args.warmup, torch)
             plans[0].sync_check(stream)
+            _progress(f"batched: {prec} grouped {ms:.1f} ms per batch")
             res[prec] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": sweeps,
                          "path": ("grouped FP32 launch per pass" if prec == "fp32" else
                                   "grouped tcgen05 CTA-pair launch per pass (tile queue over all problems)")}
-        # the same BF16x3 solves issued per plan on a pool of 8 streams (no grouping), for comparison
-        pool = [torch.cuda.Stream() for _ in range(8)]
-
+        # the same BF16x3 solves as one sem3d_solve call per plan, one after another on the stream, for comparison
         def per_plan():
-            ev = torch.cuda.Event()
-            ev.record(stream)
             for q, p in enumerate(plans):
-                pool[q % 8].wait_event(ev)
-                p.solve(fs[q], us[q], pool[q % 8])
-            for st in pool:
-                e2 = torch.cuda.Event()
-                e2.record(st)
-                stream.wait_event(e2)
+                p.solve(fs[q], us[q], stream)
 
         ms = _timed_host(per_plan, args.steps, args.warmup, torch)
         plans[0].sync_check(stream)
-        res["bf16x3_per_plan_streams"] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": 3,
-                                          "path": "each plan's sem3d_solve on a pool of 8 streams"}
+        res["bf16x3_per_plan"] = {"ms_per_batch": ms, "GDoF_per_s": dofs / (ms / 1e3) / 1e9, "sweeps": 3,
+                                  "path": "each plan's sem3d_solve in turn on one stream (no grouping)"}
+        _progress(f"batched: per-plan solves {ms:.1f} ms per batch")
         line.update({"metric": f"{args.batch_count} batched Helmholtz solves (uneven n in {{63..511}}, k in {{2,3,4,6}}): GDoF/s",
                      "value": res["bf16x3"]["GDoF_per_s"], "unit": "GDoF/s", "total_dofs": dofs, "tiers": res,
                      "steps": args.steps, "warmup": args.warmup})

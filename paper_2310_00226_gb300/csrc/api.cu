@@ -483,6 +483,10 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision prec, int sweep
     const cudaError_t e = tc_autotune(h->g, h->dev, prec == SEM3D_BF16 ? 1 : 3, h->d_err, h->num_sms);
     if (e != cudaSuccess) return fail(SEM3D_ERR_CUDA, std::string("tensor-core autotuning: ") + cudaGetErrorString(e));
   }
+  if (prec == SEM3D_TF32) {
+    const cudaError_t e = tf32_autotune(h->g, h->dev, h->d_err, h->num_sms);
+    if (e != cudaSuccess) return fail(SEM3D_ERR_CUDA, std::string("TF32 autotuning: ") + cudaGetErrorString(e));
+  }
   h->prec = prec;
   h->sweeps = sweeps;
   return SEM3D_OK;
@@ -774,7 +778,16 @@ sem3d_status sem3d_sync_check(sem3d_handle h, void* stream) {
   CUDA_TRY(cudaMemcpy(&flags, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (flags != 0) {
     CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
-    if (flags & (1 << SEM3D_ERR_TIMEOUT)) return fail(SEM3D_ERR_TIMEOUT, "a tensor-core kernel's bounded wait expired");
+    if (flags & (1 << SEM3D_ERR_TIMEOUT)) {
+      // bits 8-15: where the wait ran out (role and kernel family, see tc_ptx.cuh)
+      static const char* names[8] = {"producer", "MMA (operands)", "MMA (accumulator)", "epilogue",
+                                     "split kernel", "split CTA-pair kernel", "TF32 kernel", "TF32 CTA-pair kernel"};
+      std::string where;
+      for (int b = 0; b < 8; ++b)
+        if (flags & (1 << (8 + b))) where += std::string(where.empty() ? "" : ", ") + names[b];
+      return fail(SEM3D_ERR_TIMEOUT, "a tensor-core kernel's bounded wait expired" +
+                                         (where.empty() ? std::string() : " (" + where + ")"));
+    }
     return fail(SEM3D_ERR_CUDA, "device error flag set");
   }
   return SEM3D_OK;

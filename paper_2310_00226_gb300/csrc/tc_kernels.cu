@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
       for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t par = ((it / STAGES) & 1) ^ 1;
-        if (!mbar_wait(empty_bar(s), par, a.err)) { ok = false; break; }
+        if (!mbar_wait(empty_bar(s), par, a.err, KERN_SPLIT | WAIT_PRODUCER)) { ok = false; break; }
         const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
         const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
@@ -180,13 +180,13 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
     for (int ct = cid; ct < total_ct && ok; ct += ncl) {
       for (int kb0 = 0; kb0 < a.k_blocks; kb0 += a.kc, ++cc) {
         const int buf = cc & 1;
-        if (!mbar_wait(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+        if (!mbar_wait(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err, KERN_SPLIT | WAIT_MMA_TMEM)) { ok = false; break; }
         tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(buf * BN);
         const int kb1 = kb0 + a.kc < a.k_blocks ? kb0 + a.kc : a.k_blocks;
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % STAGES;
-          if (!mbar_wait(full_bar(s), (it / STAGES) & 1, a.err)) { ok = false; break; }
+          if (!mbar_wait(full_bar(s), (it / STAGES) & 1, a.err, KERN_SPLIT | WAIT_MMA_FULL)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
           const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
         int prev = -1;
         for (int kb0 = 0; kb0 < a.k_blocks; kb0 += a.kc, ++cc) {
           const int buf = cc & 1;
-          if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err)) { ok = false; break; }
+          if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err, KERN_SPLIT | WAIT_EPILOGUE)) { ok = false; break; }
           tc_fence_after();
           if (prev >= 0) {
 #pragma unroll 1
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(num_threads(MODE), 1)
       } else {
         const int c = cc++;  // one chunk per tile (a.kc >= a.k_blocks)
         const int buf = c & 1;
-        if (!mbar_wait(tfull_bar(buf), (c >> 1) & 1, a.err)) break;
+        if (!mbar_wait(tfull_bar(buf), (c >> 1) & 1, a.err, KERN_SPLIT | WAIT_EPILOGUE)) break;
         tc_fence_after();
 #pragma unroll 1
         for (int ch = 0; ch < COLS / 32; ++ch) {

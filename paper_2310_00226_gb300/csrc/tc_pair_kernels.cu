@@ -140,7 +140,7 @@ __device__ __forceinline__ void pair_body(const Src& src, int* err, int stall) {
       for (int kb = 0; kb < k_blocks; ++kb, ++it) {
         const int s = it % P_STAGES;
         const uint32_t par = ((it / P_STAGES) & 1) ^ 1;
-        if (!mbar_wait(empty_bar(s), par, err)) { ok = false; break; }
+        if (!mbar_wait(empty_bar(s), par, err, KERN_SPLIT_PAIR | WAIT_PRODUCER)) { ok = false; break; }
         const uint32_t st = smem_u32(smem + s * P_STAGE_BYTES);
         const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
         const uint32_t b_hi = st + 2 * A_TILE_BYTES, b_lo = b_hi + P_B_TILE_BYTES;
@@ -190,12 +190,15 @@ __device__ __forceinline__ void pair_body(const Src& src, int* err, int stall) {
       src.at(pt, cursor, t);
       const int k_blocks = t.a->k_blocks;
       const int buf = cc & 1;
-      if (!mbar_wait_cluster(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, err)) { ok = false; break; }
+      if (!mbar_wait_cluster(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, err, KERN_SPLIT_PAIR | WAIT_MMA_TMEM)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       const uint32_t tmem_d = tmem_base + (uint32_t)(buf * BN);
       for (int kb = 0; kb < k_blocks; ++kb, ++it) {
         const int s = it % P_STAGES;
-        if (!mbar_wait(full_bar(s), (it / P_STAGES) & 1, err)) { ok = false; break; }
+        if (!mbar_wait(full_bar(s), (it / P_STAGES) & 1, err, KERN_SPLIT_PAIR | WAIT_MMA_FULL)) { ok = false; break; }
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * P_STAGE_BYTES);
         const uint32_t a_hi = st, a_lo = st + A_TILE_BYTES;
@@ -236,7 +239,7 @@ __device__ __forceinline__ void pair_body(const Src& src, int* err, int stall) {
       const int row = mt * BM + quad * 32 + lane;
       const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slice * COLS);
       const int buf = cc & 1;
-      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, err)) break;
+      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, err, KERN_SPLIT_PAIR | WAIT_EPILOGUE)) break;
       tc_fence_after();
 #pragma unroll 1
       for (int ch = 0; ch < COLS / 32; ++ch) {

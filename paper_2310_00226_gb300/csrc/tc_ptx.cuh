@@ -40,11 +40,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Where a bounded wait expired, recorded beside SEM3D_ERR_TIMEOUT in the
+// device error word (read back by sem3d_sync_check): the kernel family and
+// the role whose wait ran out.
+enum : int {
+  WAIT_PRODUCER = 1 << 8,   // TMA producer waiting for a free stage
+  WAIT_MMA_FULL = 1 << 9,   // MMA issuer waiting for a stage's operands
+  WAIT_MMA_TMEM = 1 << 10,  // MMA issuer waiting for a free accumulator
+  WAIT_EPILOGUE = 1 << 11,  // epilogue waiting for a finished accumulator
+  KERN_SPLIT = 1 << 12,     // split-precision kernel, one CTA per tile
+  KERN_SPLIT_PAIR = 1 << 13,  // split-precision kernel, CTA pair (incl. grouped)
+  KERN_TF32 = 1 << 14,      // TF32 kernel, one CTA per tile
+  KERN_TF32_PAIR = 1 << 15  // TF32 kernel, CTA pair
+};
+
 // Bounded wait on an mbarrier phase.  Returns false when the wait expires
-// (recording SEM3D_ERR_TIMEOUT in *err) or, while err is non-null, when
-// another thread of the grid has already recorded an error.  err == nullptr
-// is used by the final drains: they only bound the wait.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+// (recording SEM3D_ERR_TIMEOUT and `site` in *err) or, while err is
+// non-null, when another thread of the grid has already recorded an error.
+// err == nullptr is used by the final drains: they only bound the wait.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int site = 0) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
@@ -52,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
     if ((it & 255u) == 0) {
       if (err != nullptr && *reinterpret_cast<volatile int*>(err) != 0) return false;
       if (globaltimer() - t0 > WAIT_NS) {
-        if (err != nullptr) atomicOr(err, 1 << SEM3D_ERR_TIMEOUT);
+        if (err != nullptr) atomicOr(err, (1 << SEM3D_ERR_TIMEOUT) | site);
         return false;
       }
     }
@@ -72,7 +86,7 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t par
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err, int site = 0) {
   if (mbar_try_wait_cluster(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
@@ -80,7 +94,7 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
     if ((it & 255u) == 0) {
       if (err != nullptr && *reinterpret_cast<volatile int*>(err) != 0) return false;
       if (globaltimer() - t0 > WAIT_NS) {
-        if (err != nullptr) atomicOr(err, 1 << SEM3D_ERR_TIMEOUT);
+        if (err != nullptr) atomicOr(err, (1 << SEM3D_ERR_TIMEOUT) | site);
         return false;
       }
     }

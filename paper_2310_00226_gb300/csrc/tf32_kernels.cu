@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
       const int m0 = (mg * T_CL + rank) * T_BM, n0 = nt * T_BN;
       for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
         const int s = it % T_STAGES;
-        if (!mbar_wait(empty_bar(s), ((it / T_STAGES) & 1) ^ 1, a.err)) { ok = false; break; }
+        if (!mbar_wait(empty_bar(s), ((it / T_STAGES) & 1) ^ 1, a.err, KERN_TF32 | WAIT_PRODUCER)) { ok = false; break; }
         const uint32_t st = smem_u32(smem + s * T_STAGE_BYTES);
         mbar_arrive_expect_tx(full_bar(s), T_STAGE_BYTES);
         const int k0 = kb * T_BK;
@@ -202,12 +202,12 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
     bool ok = true;
     for (int ct = cid; ct < total_ct && ok; ct += ncl, ++cc) {
       const int buf = cc & 1;
-      if (!mbar_wait(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err)) break;
+      if (!mbar_wait(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err, KERN_TF32 | WAIT_MMA_TMEM)) break;
       tc_fence_after();
       const uint32_t tmem_d = tmem_base + (uint32_t)(buf * T_BN);
       for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
         const int s = it % T_STAGES;
-        if (!mbar_wait(full_bar(s), (it / T_STAGES) & 1, a.err)) { ok = false; break; }
+        if (!mbar_wait(full_bar(s), (it / T_STAGES) & 1, a.err, KERN_TF32 | WAIT_MMA_FULL)) { ok = false; break; }
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * T_STAGE_BYTES);
 #pragma unroll
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
       const int mg = ct / a.n_tiles, nt = ct - mg * a.n_tiles;
       const int mt = mg * T_CL + rank;
       const int buf = cc & 1;
-      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err)) break;
+      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err, KERN_TF32 | WAIT_EPILOGUE)) break;
       tc_fence_after();
       const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * T_BN + slice * COLS);
       const int row = mt * T_BM + quad * 32 + lane;
@@ -338,7 +338,10 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
       const int m0 = (2 * mp + rank) * T_BM, n0 = nt * T_BN + rank * ROWS_B;
       for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
         const int s = it % TP_STAGES;
-        if (!mbar_wait(empty_bar(s), ((it / TP_STAGES) & 1) ^ 1, a.err)) { ok = false; break; }
+        if (!mbar_wait(empty_bar(s), ((it / TP_STAGES) & 1) ^ 1, a.err, KERN_TF32_PAIR | WAIT_PRODUCER)) {
+          ok = false;
+          break;
+        }
         const uint32_t st = smem_u32(smem + s * TP_STAGE_BYTES);
         const uint32_t fb = full_leader0 + 8u * s;
         if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * TP_STAGE_BYTES);
@@ -361,12 +364,12 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
     bool ok = true;
     for (int pt = pid; pt < total_pt && ok; pt += npairs, ++cc) {
       const int buf = cc & 1;
-      if (!mbar_wait_cluster(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err)) break;
+      if (!mbar_wait_cluster(tempty_bar(buf), ((cc >> 1) & 1) ^ 1, a.err, KERN_TF32_PAIR | WAIT_MMA_TMEM)) break;
       tc_fence_after();
       const uint32_t tmem_d = tmem_base + (uint32_t)(buf * T_BN);
       for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
         const int s = it % TP_STAGES;
-        if (!mbar_wait(full_bar(s), (it / TP_STAGES) & 1, a.err)) { ok = false; break; }
+        if (!mbar_wait(full_bar(s), (it / TP_STAGES) & 1, a.err, KERN_TF32_PAIR | WAIT_MMA_FULL)) { ok = false; break; }
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * TP_STAGE_BYTES);
 #pragma unroll
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(t_threads(MODE), 1)
       const int mp = pt / a.n_tiles, nt = pt - mp * a.n_tiles;
       const int mt = 2 * mp + rank;
       const int buf = cc & 1;
-      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err)) break;
+      if (!mbar_wait(tfull_bar(buf), (cc >> 1) & 1, a.err, KERN_TF32_PAIR | WAIT_EPILOGUE)) break;
       tc_fence_after();
       const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * T_BN + slice * COLS);
       const int row = mt * T_BM + quad * 32 + lane;

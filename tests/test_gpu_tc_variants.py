@@ -96,3 +96,26 @@ def test_set_tc_config_validates(sem3d):
             p.set_tc_config(3, 0)
         with pytest.raises(sem3d.Sem3dError):
             p.set_tc_config(0, 2)
+
+
+TF32_CASES = [((63, 47, 95), 4, (1.0, 0.9, 1.1), 1.5), ((287, 257, 259), 2, (1.0, 1.0, 1.0), 1.0)]
+
+
+@pytest.mark.parametrize("case", range(len(TF32_CASES)))
+def test_tf32_pair_kernel_is_bit_identical_to_single_cta_kernel(sem3d, case):
+    # The TF32 tier's two kernels (kind::tf32; one CTA per tile with W
+    # multicast, or a cta_group::2 pair) on ragged grids, bare and refined.
+    n3, k, L3, c = TF32_CASES[case]
+    F = random_rhs(*n3, seed=60 + case)
+    for sweeps in (0, 3):
+        single = _solve(sem3d, n3, k, L3, c, "tf32", sweeps, "mixed", 0, F)
+        pair = _solve(sem3d, n3, k, L3, c, "tf32", sweeps, "mixed", 1, F)
+        assert np.isfinite(pair).all()
+        assert np.array_equal(pair, single), (sweeps, float(np.abs(pair - single).max()))
+
+
+def test_tf32_autotuner_records_a_choice_per_axis(sem3d):
+    n3, k = (191, 95, 127), 4
+    with sem3d.Plan(*n3, k, (1.0, 1.0, 1.0), 1.0) as p:
+        p.set_precision("tf32", 0)
+        assert all(p.tc_config(ax) in (0, 1) for ax in range(3))
