@@ -158,11 +158,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, int row, int col
       const int rr = row < a.rows ? row : 0;  // rows past the end (not stored) read valid entries
       const int j = rr % a.ny, l = rr / a.ny;
       const float s = __ldg(a.lamy + j) + __ldg(a.lamz + l) + a.c;
+      // lambda_x of the chunk's 32 outputs: one coalesced load (lane q holds
+      // output col0 + q), broadcast by shuffles; every lane of the warp is here
+      const int lane = threadIdx.x & 31;
+      const float lx = __ldg(a.lamx + min(col0 + lane, a.nout - 1));
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const int o = col0 + q;
-        const float d = (full || o < a.nout) ? __ldg(a.lamx + o) + s : 1.0f;
-        v[q] = __fdividef(v[q], d);
+        const float d = __shfl_sync(0xFFFFFFFFu, lx, q) + s;
+        v[q] = __fdividef(v[q], (full || col0 + q < a.nout) ? d : 1.0f);
       }
     }
     if (FMT == 1 && (MODE == OUT_SPLIT || MODE == OUT_DIV_SPLIT)) {

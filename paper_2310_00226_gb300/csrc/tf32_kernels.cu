@@ -85,22 +85,28 @@ struct Tf32Args {
 };
 
 // Epilogue of one 32-column chunk: TMEM lane = `row`, v[q] = column col0 + q.
+// Every lane of the warp calls this (rows past the end return after the
+// division, whose shuffles need the whole warp).
 template <int MODE>
 __device__ __forceinline__ void tf32_epilogue(const Tf32Args& a, int row, int col0, float (&v)[32]) {
-  if (row >= a.rows) return;
+  const bool row_ok = row < a.rows;
   const bool full = col0 + 32 <= a.nout;
-  const int i1 = row % a.d1, i2 = row / a.d1;
-  const size_t cs = (size_t)a.P1 * (size_t)a.d2;
-  const size_t base = (size_t)i1 + (size_t)a.P1 * (size_t)i2 + (size_t)col0 * cs;
+  const int rowc = row_ok ? row : 0;
+  const int i1 = rowc % a.d1, i2 = rowc / a.d1;
   if (MODE == T_OUT_T32_DIV) {
     const float s = __ldg(a.lam1 + i1) + __ldg(a.lam2 + i2) + a.c;
+    // lam3 of the chunk's 32 outputs: one coalesced load, broadcast by shuffles
+    const int lane = threadIdx.x & 31;
+    const float l3 = __ldg(a.lam3 + min(col0 + lane, a.nout - 1));
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
-      const int o = col0 + q;
-      const float d = (full || o < a.nout) ? s + __ldg(a.lam3 + o) : 1.0f;
-      v[q] = __fdividef(v[q], d);
+      const float d = s + __shfl_sync(0xFFFFFFFFu, l3, q);
+      v[q] = __fdividef(v[q], (full || col0 + q < a.nout) ? d : 1.0f);
     }
   }
+  if (!row_ok) return;
+  const size_t cs = (size_t)a.P1 * (size_t)a.d2;
+  const size_t base = (size_t)i1 + (size_t)a.P1 * (size_t)i2 + (size_t)col0 * cs;
   if (MODE == T_OUT_T32 || MODE == T_OUT_T32_DIV) {
     float* p = a.out32 + base;
 #pragma unroll

@@ -116,3 +116,30 @@ def test_grouped_tensor_core_batch_is_bit_identical_to_single_solves(sem3d, tier
     finally:
         for p in plans:
             p.close()
+
+
+def test_grouped_neumann_batch_is_bit_identical_to_single_solves(sem3d):
+    # Neumann plans (every GLL node kept, n = Ne*k + 1) take the grouped
+    # tensor-core path with FP64 residuals in every sweep (per-row stencil);
+    # sizes give ragged M, N and K tiles.
+    shapes = [((129, 65, 97), 4, 2.0), ((97, 97, 33), 2, 1.0), ((41, 161, 81), 4, 5.0)]
+    plans, fs, us, ref = [], [], [], []
+    try:
+        for q, (n3, k, c) in enumerate(shapes):
+            p = sem3d.Plan(*n3, k, (1.0, 1.0, 1.0), c, bc="neumann")
+            p.set_precision("bf16x3", 3)
+            f = torch.from_numpy(random_rhs(*n3, seed=90 + q)).cuda()
+            u = torch.empty_like(f)
+            p.solve(f, u)
+            p.sync_check()
+            plans.append(p)
+            fs.append(f)
+            ref.append(u.cpu().numpy())
+            us.append(torch.full_like(f, float("nan")))
+        sem3d.solve_batched(plans, fs, us)
+        plans[0].sync_check()
+        for q in range(len(shapes)):
+            assert np.array_equal(us[q].cpu().numpy(), ref[q]), q
+    finally:
+        for p in plans:
+            p.close()
