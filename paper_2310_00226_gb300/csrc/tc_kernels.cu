@@ -338,7 +338,8 @@ template <int PASS, int MODE, int NP, int FMT = 0>
 cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                       const TcArgs& a, long long work_clusters, int num_sms, cudaStream_t s) {
   auto kern = mode_product_bf16x3_kernel<PASS, MODE, CLUSTER, NP, FMT>;
-  static int max_clusters = 0;  // per instantiation: co-resident clusters of CLUSTER CTAs
+  static std::atomic<int> max_clusters_cache{0};  // per instantiation: co-resident clusters of CLUSTER CTAs
+  int max_clusters = max_clusters_cache.load(std::memory_order_relaxed);
   if (max_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PASS));
     if (e != cudaSuccess) return e;
@@ -362,6 +363,7 @@ cudaError_t launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtens
     } else {
       max_clusters = num_sms;
     }
+    max_clusters_cache.store(max_clusters, std::memory_order_relaxed);
   }
   const long long clusters = work_clusters < max_clusters ? work_clusters : max_clusters;
   cudaLaunchConfig_t cfg = {};

@@ -6,6 +6,7 @@
 #include "tc_common.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace sem3d {
 
@@ -293,7 +294,7 @@ template <int PASS, int MODE, int NP>
 cudaError_t launch_tc_pair(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                            const TcArgs& a, long long work_pairs, int num_sms, cudaStream_t s) {
   auto kern = mode_product_bf16x3_pair_kernel<PASS, MODE, NP>;
-  static int max_pairs = 0;  // per instantiation: co-resident clusters of 2 CTAs
+  static std::atomic<int> max_pairs_cache{0};  // per instantiation: co-resident clusters of 2 CTAs
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -304,6 +305,7 @@ cudaError_t launch_tc_pair(const CUtensorMap& a0, const CUtensorMap& a1, const C
   cfg.dynamicSmemBytes = pair_smem_bytes(PASS);
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int max_pairs = max_pairs_cache.load(std::memory_order_relaxed);
   if (max_pairs == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes(PASS));
     if (e != cudaSuccess) return e;
@@ -313,6 +315,7 @@ cudaError_t launch_tc_pair(const CUtensorMap& a0, const CUtensorMap& a1, const C
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_pairs = n;
+    max_pairs_cache.store(n, std::memory_order_relaxed);
   }
   const long long pairs = work_pairs < max_pairs ? work_pairs : max_pairs;
   cfg.gridDim = dim3((unsigned)(2 * pairs));
@@ -353,7 +356,7 @@ template <int PASS, int MODE, int NP>
 cudaError_t launch_pair_group_t(const TcGroupEntry* tab, int count, int total, int* err, int stall, int num_sms,
                                 cudaStream_t s) {
   auto kern = mode_product_bf16x3_pair_group_kernel<PASS, MODE, NP>;
-  static int max_pairs = 0;
+  static std::atomic<int> max_pairs_cache{0};
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -364,6 +367,7 @@ cudaError_t launch_pair_group_t(const TcGroupEntry* tab, int count, int total, i
   cfg.dynamicSmemBytes = pair_smem_bytes(PASS);
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int max_pairs = max_pairs_cache.load(std::memory_order_relaxed);
   if (max_pairs == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes(PASS));
     if (e != cudaSuccess) return e;
@@ -373,6 +377,7 @@ cudaError_t launch_pair_group_t(const TcGroupEntry* tab, int count, int total, i
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_pairs = n;
+    max_pairs_cache.store(n, std::memory_order_relaxed);
   }
   const int pairs = total < max_pairs ? total : max_pairs;
   cfg.gridDim = dim3((unsigned)(2 * pairs));

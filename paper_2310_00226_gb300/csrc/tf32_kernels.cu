@@ -27,6 +27,7 @@
 #include "tc_ptx.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -455,7 +456,7 @@ template <int MODE>
 cudaError_t launch_tf32(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32Args& a, long long work_clusters,
                         int num_sms, cudaStream_t s) {
   auto kern = mode_product_tf32_kernel<MODE>;
-  static int max_clusters = 0;  // co-resident clusters of this instantiation
+  static std::atomic<int> max_clusters_cache{0};  // co-resident clusters of this instantiation
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -466,6 +467,7 @@ cudaError_t launch_tf32(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32
   cfg.dynamicSmemBytes = T_SMEM;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int max_clusters = max_clusters_cache.load(std::memory_order_relaxed);
   if (max_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM);
     if (e != cudaSuccess) return e;
@@ -475,6 +477,7 @@ cudaError_t launch_tf32(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_clusters = n;
+    max_clusters_cache.store(n, std::memory_order_relaxed);
   }
   const long long clusters = work_clusters < max_clusters ? work_clusters : max_clusters;
   cfg.gridDim = dim3((unsigned)(clusters * T_CL));
@@ -486,7 +489,7 @@ template <int MODE>
 cudaError_t launch_tf32_pair(const CUtensorMap& mA, const CUtensorMap& mB, const Tf32Args& a, long long work_pairs,
                              int num_sms, cudaStream_t s) {
   auto kern = mode_product_tf32_pair_kernel<MODE>;
-  static int max_pairs = 0;
+  static std::atomic<int> max_pairs_cache{0};
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -497,6 +500,7 @@ cudaError_t launch_tf32_pair(const CUtensorMap& mA, const CUtensorMap& mB, const
   cfg.dynamicSmemBytes = TP_SMEM;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int max_pairs = max_pairs_cache.load(std::memory_order_relaxed);
   if (max_pairs == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM);
     if (e != cudaSuccess) return e;
@@ -506,6 +510,7 @@ cudaError_t launch_tf32_pair(const CUtensorMap& mA, const CUtensorMap& mB, const
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_pairs = n;
+    max_pairs_cache.store(n, std::memory_order_relaxed);
   }
   const long long pairs = work_pairs < max_pairs ? work_pairs : max_pairs;
   cfg.gridDim = dim3((unsigned)(2 * pairs));
