@@ -1150,6 +1150,22 @@ sem3d_status batch_resources(int device, size_t stages) {
   return SEM3D_OK;
 }
 
+// Marks the last use of the staging area on s when a grouped batch returns,
+// on its error paths too, so that the next batch waits for every table copy
+// this one queued before it rewrites the pinned host tables.
+struct StagingRelease {
+  cudaStream_t s;
+  bool recorded = false;
+  sem3d_status record() {
+    recorded = true;
+    CUDA_TRY(cudaEventRecord(g_batch.done, s));
+    return SEM3D_OK;
+  }
+  ~StagingRelease() {
+    if (!recorded) cudaEventRecord(g_batch.done, s);
+  }
+};
+
 // Grouped FP32 solves: each of the six passes of all problems is one launch.
 sem3d_status batched_f32(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
                          cudaStream_t s) {
@@ -1157,6 +1173,7 @@ sem3d_status batched_f32(int count, const sem3d_handle* hs, const double* const*
   const size_t stages = 6 * (size_t)(1 + sweeps);
   sem3d_status st = batch_resources(hs[0]->device, stages);
   if (st != SEM3D_OK) return st;
+  StagingRelease release{s};
   std::vector<Geom> geo(count);
   std::vector<const float*> W(count);
   std::vector<const void*> in(count);
@@ -1210,8 +1227,7 @@ sem3d_status batched_f32(int count, const sem3d_handle* hs, const double* const*
     }
     if ((st = solve_group([&](int q) -> const void* { return R[q]; }, true)) != SEM3D_OK) return st;
   }
-  CUDA_TRY(cudaEventRecord(g_batch.done, s));
-  return SEM3D_OK;
+  return release.record();
 }
 
 // Any tiers: each problem's own solve on a pool of streams, forked from and
@@ -1271,6 +1287,7 @@ sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* 
   const int nprod = hs[0]->prec == SEM3D_BF16 ? 1 : 3;
   sem3d_status st = batch_resources(hs[0]->device, 6 * (size_t)(1 + sweeps));
   if (st != SEM3D_OK) return st;
+  StagingRelease release{s};
   StreamFan fan;
   if ((st = fan.init(s, count)) != SEM3D_OK) return st;
   std::vector<TcBuffers> S0(count), S1(count);
@@ -1352,8 +1369,7 @@ sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* 
     if ((st = fan.end()) != SEM3D_OK) return st;
     if ((st = solve_group(EPI_ACCUM, true, false)) != SEM3D_OK) return st;
   }
-  CUDA_TRY(cudaEventRecord(g_batch.done, s));
-  return SEM3D_OK;
+  return release.record();
 }
 
 sem3d_status batched_streams(int count, const sem3d_handle* hs, const double* const* f, double* const* u,
