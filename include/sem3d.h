@@ -151,6 +151,33 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
 typedef enum { SEM3D_RESIDUAL_FP64 = 0, SEM3D_RESIDUAL_MIXED = 1, SEM3D_RESIDUAL_DF = 2 } sem3d_residual;
 sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode);
 
+/* How the split tiers (SEM3D_BF16X3, SEM3D_BF16) evaluate their FP64-accurate
+ * residuals (every sweep of SEM3D_RESIDUAL_FP64, the last sweep of
+ * SEM3D_RESIDUAL_MIXED) -- the same r = f - (c + H_x (+) H_y (+) H_z) u of
+ * Eq. 12 either way:
+ *   SEM3D_EXACT_FIXED : (default) exactly in 64-bit integer fixed point on
+ *                       the integer pipe: u and f scaled by one power of two
+ *                       per field (found on the device from their largest
+ *                       exponents) to 58 / 61-bit integers, the rows of H to
+ *                       integers whose magnitudes over a node's terms sum to
+ *                       ~2^58; products and sums are exact, and the
+ *                       truncations and dropped low partial products leave
+ *                       an absolute error below 2^-53 of the largest
+ *                       sum of |H||u| over the grid -- within one FP64
+ *                       rounding of that sum (normwise: nodes where |u| is
+ *                       far below max |u| get the field's absolute
+ *                       resolution).
+ *                       Dirichlet plans with k in {1, 2, 4}; other plans use
+ *                       FP64 arithmetic.  Inf or NaN in u or f gives a NaN
+ *                       residual.
+ *   SEM3D_EXACT_FP64  : FP64 fused multiply-adds.
+ * sem3d_exact_residual_kind reports the arithmetic the plan's current tier
+ * and geometry use (SEM3D_EXACT_FP64 for tiers other than the split ones).
+ * Errors: SEM3D_ERR_INVALID_ARG for a NULL handle / pointer or unknown kind. */
+typedef enum { SEM3D_EXACT_FIXED = 0, SEM3D_EXACT_FP64 = 1 } sem3d_exact_residual;
+sem3d_status sem3d_set_exact_residual(sem3d_handle h, sem3d_exact_residual kind);
+sem3d_status sem3d_exact_residual_kind(sem3d_handle h, int* kind);
+
 /* Bytes of device workspace that sem3d_solve needs in the current mode. */
 sem3d_status sem3d_workspace_size(sem3d_handle h, size_t* bytes);
 

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsem3d.so")
-SOURCES = ["api.cu", "fp64_kernels.cu", "fp32_kernels.cu", "tc_kernels.cu", "tc_pair_kernels.cu", "tf32_kernels.cu", "pcg_kernels.cu", "ch_kernels.cu", "setup1d.cpp"]
+SOURCES = ["api.cu", "fp64_kernels.cu", "fix_kernels.cu", "fp32_kernels.cu", "tc_kernels.cu", "tc_pair_kernels.cu", "tf32_kernels.cu", "pcg_kernels.cu", "ch_kernels.cu", "setup1d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -69,6 +69,12 @@ struct sem3d_plan {
   sem3d_precision prec = SEM3D_FP64;
   int sweeps = 1;
   int residual = SEM3D_RESIDUAL_MIXED;  // arithmetic of the refinement residuals (BF16X3 tier)
+  // FP64-accurate residuals of the split tiers: 64-bit fixed point on the
+  // integer pipe (fix_ok: Dirichlet, k in {1, 2, 4}) unless exact_kind says FP64
+  FixCoef fix{};
+  bool fix_ok = false;
+  int exact_kind = SEM3D_EXACT_FIXED;
+  int* d_fix = nullptr;  // 2 ints: max exponents of u and f
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -365,6 +371,7 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
   p->g.nx = nx; p->g.ny = ny; p->g.nz = nz; p->g.Px = pad16(nx); p->g.c = c; p->g.bc = (int)bc;
   p->k = k;
   for (int a = 0; a < 3; ++a) p->L[a] = L3[a];
+  std::vector<double> hq_rows[3];
   for (int a = 0; a < 3; ++a) {
     const Axis1D& A = *p->ax[a];
     DevAxis& D = p->dev[a];
@@ -378,7 +385,8 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
     if ((st = dev_upload(p.get(), &D.lamf, lf.data(), lf.size())) != SEM3D_OK) return st;
     if ((st = dev_upload(p.get(), &D.Hband, A.Hband.data(), A.Hband.size())) != SEM3D_OK) return st;
     {
-      std::vector<double> hq = A.Hq;  // the shift c joins the x operator's diagonal
+      std::vector<double>& hq = hq_rows[a];
+      hq = A.Hq;  // the shift c joins the x operator's diagonal
       if (a == 0)
         for (int q = 0; q < k; ++q) hq[(size_t)q * (2 * k + 1) + k] += c;
       if ((st = dev_upload(p.get(), &D.Hq, hq.data(), hq.size())) != SEM3D_OK) return st;
@@ -455,6 +463,11 @@ sem3d_status sem3d_setup_bc(int nx, int ny, int nz, int k, double Lx, double Ly,
     CUDA_TRY(cudaMemset(d, 0, 256));
     p->d_err = static_cast<int*>(d);
     p->d_f16 = reinterpret_cast<F16State*>(static_cast<char*>(d) + 128);
+    p->d_fix = reinterpret_cast<int*>(static_cast<char*>(d) + 192);
+  }
+  if (p->g.bc == 0) {
+    const double* rows[3] = {hq_rows[0].data(), hq_rows[1].data(), hq_rows[2].data()};
+    p->fix_ok = build_fix_coef(rows, k, p->fix);
   }
   p->div_bound = (float)(1.0 / (lmin + c));
   *out = p.release();
@@ -545,6 +558,20 @@ sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode) {
   return SEM3D_OK;
 }
 
+sem3d_status sem3d_set_exact_residual(sem3d_handle h, sem3d_exact_residual kind) {
+  if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
+  if (kind != SEM3D_EXACT_FIXED && kind != SEM3D_EXACT_FP64) return fail(SEM3D_ERR_INVALID_ARG, "unknown kind");
+  h->exact_kind = kind;
+  return SEM3D_OK;
+}
+
+sem3d_status sem3d_exact_residual_kind(sem3d_handle h, int* kind) {
+  if (!h || !kind) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
+  const bool split = h->prec == SEM3D_BF16X3 || h->prec == SEM3D_BF16;
+  *kind = (split && h->fix_ok && h->exact_kind == SEM3D_EXACT_FIXED) ? SEM3D_EXACT_FIXED : SEM3D_EXACT_FP64;
+  return SEM3D_OK;
+}
+
 sem3d_status sem3d_workspace_size(sem3d_handle h, size_t* bytes) {
   if (!h || !bytes) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
   *bytes = workspace_bytes(h);
@@ -621,6 +648,11 @@ sem3d_status sem3d_solve_host_wait(sem3d_handle h, void* stream) {
 namespace {
 
 // The solve itself (arguments already checked, workspace present).
+// FP64-accurate residuals of the split tiers in 64-bit fixed point (see fix_kernels.cu)
+bool use_fixed_residual(const sem3d_plan* h) {
+  return h->fix_ok && h->exact_kind == SEM3D_EXACT_FIXED && (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_BF16);
+}
+
 sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s) {
   const size_t N = (size_t)h->g.nx * h->g.ny * h->g.nz;
   sem3d_status st = SEM3D_OK;
@@ -707,11 +739,19 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
           return st;
       }
     }
+    const bool fixed = use_fixed_residual(h);
+    bool f_exp_known = false;  // max exponent of f, found by the first fixed-point residual
     for (int q = ndf; q < sw; ++q) {
       if (f16) {
         if ((st = reset_scales()) != SEM3D_OK) return st;
         LAUNCH(h, K_STENCIL, 1, s, launch_stencil_f32out(h->g, h->k, h->dev, u, f, r32, h->d_f16, s));
         LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
+      } else if (fixed) {
+        // the double-FP32 solution buffers are free by now: they hold u in fixed point
+        LAUNCH(h, K_STENCIL, f_exp_known ? 3 : 4, s,
+               launch_residual_fixed(h->g, h->k, h->fix, u, f, h->d_fix, f_exp_known, reinterpret_cast<int*>(D.hi),
+                                     reinterpret_cast<int*>(D.lo), S0.hi, S0.lo, h->num_sms, s));
+        f_exp_known = true;
       } else {
         LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
                launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
@@ -1363,8 +1403,15 @@ sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* 
     if ((st = fan.begin()) != SEM3D_OK) return st;
     for (int q = 0; q < count; ++q) {
       sem3d_plan* h = hs[q];
-      LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, fan.stream(q),
-             launch_stencil(h->g, h->k, h->dev, u[q], f[q], nullptr, S0[q].hi, S0[q].lo, 2, fan.stream(q)));
+      if (use_fixed_residual(h)) {
+        const bool known = sw > ndf;
+        LAUNCH(h, K_STENCIL, known ? 3 : 4, fan.stream(q),
+               launch_residual_fixed(h->g, h->k, h->fix, u[q], f[q], h->d_fix, known, reinterpret_cast<int*>(D[q].hi),
+                                     reinterpret_cast<int*>(D[q].lo), S0[q].hi, S0[q].lo, h->num_sms, fan.stream(q)));
+      } else {
+        LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, fan.stream(q),
+               launch_stencil(h->g, h->k, h->dev, u[q], f[q], nullptr, S0[q].hi, S0[q].lo, 2, fan.stream(q)));
+      }
     }
     if ((st = fan.end()) != SEM3D_OK) return st;
     if ((st = solve_group(EPI_ACCUM, true, false)) != SEM3D_OK) return st;

@@ -216,6 +216,52 @@ cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers
 // (the F16X3 tier then splits it with launch_split_f16).  1 <= k <= 8.
 cudaError_t launch_stencil_f32out(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f,
                                   float* out32, F16State* st, cudaStream_t s);
+// ---- fixed-point residual (fix_kernels.cu)
+// Terms of the row of H with local index q (0 = element vertex) for k in
+// {1, 2, 4}: the vertex row and, for even k, the midpoint row are mirror-
+// symmetric and enter as C (U_{+d} + U_{-d}) plus a correction for the
+// rounding difference of the two FP64 entries; the other rows term by term.
+// Term e reads offset fix_da (and fix_db for a mirrored pair, else kNoRow).
+constexpr int kNoRow = -100;
+__host__ __device__ constexpr bool fix_folded(int K, int q) { return q == 0 || (K % 2 == 0 && 2 * q == K); }
+__host__ __device__ constexpr int fix_terms(int K, int q) { return q == 0 ? K + 1 : fix_folded(K, q) ? K / 2 + 1 : K + 1; }
+__host__ __device__ constexpr int fix_da(int K, int q, int e) { return fix_folded(K, q) ? e : e - q; }
+__host__ __device__ constexpr int fix_db(int K, int q, int e) { return (fix_folded(K, q) && e > 0) ? -e : kNoRow; }
+// Rows of (c +) H per axis as fixed-point integers C = round(H 2^t) (one t
+// for all axes: the terms of any node sum to about 2^58 in magnitude),
+// in balanced 28-bit chunks C = ch 2^28 + cl, entry [q * (2k+1) + e] for term
+// e; e = round((H 2^t - C) 2^14), the rounded fraction; for a mirrored pair
+// dc = C_{-d} - C_{+d} and eb the fraction of C_{-d}.  A kernel parameter.
+struct FixCoef {
+  int ch[3][4 * 9];
+  int cl[3][4 * 9];
+  int dc[3][4 * 9];
+  int e[3][4 * 9];
+  int eb[3][4 * 9];
+  int t;
+};
+struct FixArgs {
+  const int* Uh;
+  const int* Ul;
+  const double* f;
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  const int* state;  // [0]: max biased exponent of u, [1]: of f
+  int nx, ny, nz, Px;
+};
+// Build the tables from the FP64 rows hq[axis] (k x (2k+1), x with c on its
+// diagonal).  False for k not in {1, 2, 4} or rows that are not mirror-
+// symmetric up to rounding (the fixed-point residual is then not used).
+bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf);
+// r = f - (c + H_x (+) H_y (+) H_z) u evaluated exactly in 64-bit integer
+// fixed point (error below FP64 rounding of the terms), written as bf16 hi/lo
+// at pitch Px with zero pads, like launch_stencil mode 2.  Dirichlet rows and
+// k in {1, 2, 4} only (cudaErrorInvalidValue otherwise).  state: 2 device ints
+// (the max exponents of u and f; f's is reused when f_exponent_known); Uh,
+// Ul: two int32 arrays of Px * ny * nz (the fixed-point u, 16-byte aligned).
+cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const double* u, const double* f,
+                                  int* state, bool f_exponent_known, int* Uh, int* Ul, __nv_bfloat16* out_hi,
+                                  __nv_bfloat16* out_lo, int num_sms, cudaStream_t s);
 // FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads.
 cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 

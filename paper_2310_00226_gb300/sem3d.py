@@ -28,6 +28,8 @@ EXPORTS = (
     "sem3d_setup_bc",
     "sem3d_set_precision",
     "sem3d_set_residual",
+    "sem3d_set_exact_residual",
+    "sem3d_exact_residual_kind",
     "sem3d_workspace_size",
     "sem3d_set_workspace",
     "sem3d_solve",
@@ -79,6 +81,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(c_void_p)]
     L.sem3d_set_precision.argtypes = [c_void_p, c_int, c_int]
     L.sem3d_set_residual.argtypes = [c_void_p, c_int]
+    L.sem3d_set_exact_residual.argtypes = [c_void_p, c_int]
+    L.sem3d_exact_residual_kind.argtypes = [c_void_p, ctypes.POINTER(c_int)]
     L.sem3d_workspace_size.argtypes = [c_void_p, ctypes.POINTER(c_size_t)]
     L.sem3d_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
     L.sem3d_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
@@ -193,6 +197,18 @@ class Plan:
 
     def set_residual(self, mode: str = "mixed"):
         _check(lib().sem3d_set_residual(self._h, self.RESIDUALS[mode]), "sem3d_set_residual")
+
+    EXACT = {"fixed": 0, "fp64": 1}
+
+    def set_exact_residual(self, kind: str = "fixed"):
+        """Arithmetic of the split tiers' FP64-accurate residuals: "fixed"
+        (64-bit integer fixed point) or "fp64" (FP64 FMAs)."""
+        _check(lib().sem3d_set_exact_residual(self._h, self.EXACT[kind]), "sem3d_set_exact_residual")
+
+    def exact_residual_kind(self) -> str:
+        k = ctypes.c_int()
+        _check(lib().sem3d_exact_residual_kind(self._h, ctypes.byref(k)), "sem3d_exact_residual_kind")
+        return {v: n for n, v in self.EXACT.items()}[k.value]
 
     def workspace_size(self) -> int:
         b = ctypes.c_size_t()
