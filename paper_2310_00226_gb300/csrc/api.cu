@@ -709,12 +709,15 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
       CUDA_TRY(cudaMemsetAsync(h->d_f16, 0, sizeof(F16State), s));
       return SEM3D_OK;
     };
+    const bool fixed = use_fixed_residual(h);
     if (f16) {
       if ((st = reset_scales()) != SEM3D_OK) return st;
       LAUNCH(h, K_SPLIT, 1, s, launch_absmax_f64(h->g, f, h->d_f16, s));
       LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, f, true, S0h, S0l, h->d_f16, s));
     } else {
-      LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s));
+      // the fixed-point residuals' scale of f comes with the split
+      if (fixed) CUDA_TRY(cudaMemsetAsync(h->d_fix + 1, 0, sizeof(int), s));
+      LAUNCH(h, K_SPLIT, 1, s, launch_split(h->g, f, S0.hi, S0.lo, s, fixed ? h->d_fix + 1 : nullptr));
     }
     if (!mixed) {
       if ((st = solve_once_bf16x3(h, S0, S1, u, EPI_STORE, none, s)) != SEM3D_OK) return st;
@@ -739,8 +742,6 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
           return st;
       }
     }
-    const bool fixed = use_fixed_residual(h);
-    bool f_exp_known = false;  // max exponent of f, found by the first fixed-point residual
     for (int q = ndf; q < sw; ++q) {
       if (f16) {
         if ((st = reset_scales()) != SEM3D_OK) return st;
@@ -748,10 +749,9 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
         LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
       } else if (fixed) {
         // the double-FP32 solution buffers are free by now: they hold u in fixed point
-        LAUNCH(h, K_STENCIL, f_exp_known ? 3 : 4, s,
-               launch_residual_fixed(h->g, h->k, h->fix, u, f, h->d_fix, f_exp_known, reinterpret_cast<int*>(D.hi),
+        LAUNCH(h, K_STENCIL, 3, s,
+               launch_residual_fixed(h->g, h->k, h->fix, u, f, h->d_fix, true, reinterpret_cast<int*>(D.hi),
                                      reinterpret_cast<int*>(D.lo), S0.hi, S0.lo, h->num_sms, s));
-        f_exp_known = true;
       } else {
         LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, s,
                launch_stencil(h->g, h->k, h->dev, u, f, nullptr, S0.hi, S0.lo, 2, s));
@@ -1377,8 +1377,11 @@ sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* 
   };
   // f -> split input of every problem
   if ((st = fan.begin()) != SEM3D_OK) return st;
-  for (int q = 0; q < count; ++q)
-    LAUNCH(hs[q], K_SPLIT, 1, fan.stream(q), launch_split(hs[q]->g, f[q], S0[q].hi, S0[q].lo, fan.stream(q)));
+  for (int q = 0; q < count; ++q) {
+    int* fexp = use_fixed_residual(hs[q]) ? hs[q]->d_fix + 1 : nullptr;  // the fixed-point residuals' scale of f
+    if (fexp) CUDA_TRY(cudaMemsetAsync(fexp, 0, sizeof(int), fan.stream(q)));
+    LAUNCH(hs[q], K_SPLIT, 1, fan.stream(q), launch_split(hs[q]->g, f[q], S0[q].hi, S0[q].lo, fan.stream(q), fexp));
+  }
   if ((st = fan.end()) != SEM3D_OK) return st;
   if (ndf == 0) {
     if ((st = solve_group(EPI_STORE, true, false)) != SEM3D_OK) return st;
@@ -1404,9 +1407,8 @@ sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* 
     for (int q = 0; q < count; ++q) {
       sem3d_plan* h = hs[q];
       if (use_fixed_residual(h)) {
-        const bool known = sw > ndf;
-        LAUNCH(h, K_STENCIL, known ? 3 : 4, fan.stream(q),
-               launch_residual_fixed(h->g, h->k, h->fix, u[q], f[q], h->d_fix, known, reinterpret_cast<int*>(D[q].hi),
+        LAUNCH(h, K_STENCIL, 3, fan.stream(q),
+               launch_residual_fixed(h->g, h->k, h->fix, u[q], f[q], h->d_fix, true, reinterpret_cast<int*>(D[q].hi),
                                      reinterpret_cast<int*>(D[q].lo), S0[q].hi, S0[q].lo, h->num_sms, fan.stream(q)));
       } else {
         LAUNCH(h, K_STENCIL, h->g.Px != h->g.nx ? 2 : 1, fan.stream(q),

@@ -159,7 +159,7 @@ __device__ __forceinline__ void fx1(long long& P2, long long& P1, int ch, int cl
 // folding are known at compile time.  The y and z rows depend on the warp's
 // (j, l) and are read from the term tables.
 template <int K>
-__global__ void __launch_bounds__(256, 2) stencil_fix4_kernel(FixArgs a, const __grid_constant__ FixCoef cf) {
+__global__ void __launch_bounds__(256, 4) stencil_fix4_kernel(FixArgs a, const __grid_constant__ FixCoef cf) {
   constexpr int BW = 2 * K + 1;
   const int lane = threadIdx.x & 31;
   const long long lines = (long long)a.ny * a.nz;

@@ -649,9 +649,12 @@ __global__ void zero_pads_kernel(__nv_bfloat16* hi, __nv_bfloat16* lo, int nx, i
 // hi = bf16(x), lo = bf16(x - hi), x rounded to FP32 first.  Blocks walk the
 // (j, l) lines; a lane converts 4 consecutive entries and writes them as one
 // 8-byte store per array (rows of pitch Px, a multiple of 16, are aligned).
+// With emax set, the largest biased FP64 exponent of the input also goes to
+// *emax (atomicMax; the fixed-point residual's scale of f).
 __global__ void __launch_bounds__(256) split_kernel(const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, int nx,
-                                                    int Px, long long lines) {
+                                                    int Px, long long lines, int* emax) {
   const int chunks = Px >> 2;
+  unsigned int m = 0;
   for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
     const double* row = in + line * nx;
     uint2* hrow = reinterpret_cast<uint2*>(hi + line * Px);
@@ -661,7 +664,10 @@ __global__ void __launch_bounds__(256) split_kernel(const double* in, __nv_bfloa
 #pragma unroll
       for (int p = 0; p < 4; p += 2) {
         const int i = 4 * c + p;
-        const float x0 = i < nx ? f64_to_f32_rn(row[i]) : 0.f, x1 = i + 1 < nx ? f64_to_f32_rn(row[i + 1]) : 0.f;
+        const double d0 = i < nx ? row[i] : 0.0, d1 = i + 1 < nx ? row[i + 1] : 0.0;
+        m = max(m, max((unsigned int)(__double_as_longlong(d0) >> 52) & 0x7FFu,
+                       (unsigned int)(__double_as_longlong(d1) >> 52) & 0x7FFu));
+        const float x0 = f64_to_f32_rn(d0), x1 = f64_to_f32_rn(d1);
         const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
         const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
         const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
@@ -671,6 +677,10 @@ __global__ void __launch_bounds__(256) split_kernel(const double* in, __nv_bfloa
       hrow[c] = make_uint2(hw[0], hw[1]);
       lrow[c] = make_uint2(lw[0], lw[1]);
     }
+  }
+  if (emax) {  // every lane of the block gets here
+    m = __reduce_max_sync(0xFFFFFFFFu, m);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(emax, (int)m);
   }
 }
 
@@ -843,10 +853,11 @@ cudaError_t launch_split_f16(const Geom& g, const void* in, bool in_f64, __half*
   return cudaGetLastError();
 }
 
-cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,
+                         int* emax) {
   const long long lines = (long long)g.ny * g.nz;
   const long long blocks = lines < 152LL * 16 ? (lines < 1 ? 1 : lines) : 152LL * 16;
-  split_kernel<<<(int)blocks, 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines);
+  split_kernel<<<(int)blocks, 256, 0, s>>>(in, hi, lo, g.nx, g.Px, lines, emax);
   return cudaGetLastError();
 }
 

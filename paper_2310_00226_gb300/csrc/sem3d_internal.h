@@ -257,13 +257,16 @@ bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf);
 // fixed point (error below FP64 rounding of the terms), written as bf16 hi/lo
 // at pitch Px with zero pads, like launch_stencil mode 2.  Dirichlet rows and
 // k in {1, 2, 4} only (cudaErrorInvalidValue otherwise).  state: 2 device ints
-// (the max exponents of u and f; f's is reused when f_exponent_known); Uh,
+// (the max exponents of u and f; f's is taken as given when f_exponent_known,
+// e.g. from launch_split's emax); Uh,
 // Ul: two int32 arrays of Px * ny * nz (the fixed-point u, 16-byte aligned).
 cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const double* u, const double* f,
                                   int* state, bool f_exponent_known, int* Uh, int* Ul, __nv_bfloat16* out_hi,
                                   __nv_bfloat16* out_lo, int num_sms, cudaStream_t s);
-// FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads.
-cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+// FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads; with emax
+// set, also atomicMax(*emax, largest biased FP64 exponent of the input).
+cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,
+                         int* emax = nullptr);
 
 // ---- tcgen05 kernels (tc_kernels.cu)
 struct TcBuffers {

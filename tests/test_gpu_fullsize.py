@@ -257,10 +257,16 @@ def test_batched_64_problems_full_size(sem3d):
     # The oracle's full refined solve on the problems small enough for the host.
     small = [i for i, p in enumerate(plans) if p.numel <= 2_100_000]
     refs = {i: refined_solve(fs[i].cpu().numpy(), *axes[i], probs[i]["c"], 1) for i in small}
+    # Componentwise backward error: FP64-FMA residuals hold 1e-14; the fixed-
+    # point residual's resolution is absolute (one scale per field), so nodes
+    # where |u| is far below max |u| see a larger relative error: bound 5e-14
+    # (measured 1.2e-14; its normwise error is at FP64's level).
     try:
-        for tier, sweeps in (("fp32", 2), ("bf16x3", 3)):
+        for tier, sweeps, exact, bound in (("fp32", 2, "fp64", 1e-14), ("bf16x3", 3, "fp64", 1e-14),
+                                           ("bf16x3", 3, "fixed", 5e-14)):
             for p in plans:
                 p.set_precision(tier, sweeps)
+                p.set_exact_residual(exact)
             for u in us:
                 u.fill_(float("nan"))
             sem3d.solve_batched(plans, fs, us)
@@ -270,7 +276,8 @@ def test_batched_64_problems_full_size(sem3d):
                 sx, sy, sz = axes[i]
                 pairs = _lines(sy.n, sz.n, 1, seed=1000 + i)
                 worst = max(worst, _backward_error(us[i], fs[i], sx, sy, sz, pr["c"], pairs, pr["k"]))
-            assert worst < 1e-14, (tier, worst)
+            print(f"batched {tier} {sweeps} sweeps, {exact} residuals: componentwise backward error {worst:.3g}")
+            assert worst < bound, (tier, exact, worst)
             for i in small:
                 got = us[i].cpu().numpy()
                 assert np.abs(got - refs[i]).max() / np.abs(refs[i]).max() < 1e-12, (tier, i)
