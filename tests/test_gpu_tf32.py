@@ -13,7 +13,12 @@ of the inputs and matrices dominates).  An independent rounding is not close at 
 instead of rounding gives a 2-norm distance of 6.4x the TF32 error, bf16
 rounding 7.9x.  Bounds: ||gpu - oracle||_2 <= 0.5 ||oracle - exact||_2, and the
 max-norm error against the exact discrete solution within [0.6, 1.6] of the
-oracle's.  With FP64 refinement sweeps the tier converges like any other:
+oracle's.  Element by element where no rounding can flip: on grids and seeds
+whose every TF32-rounded intermediate lies farther from a rounding boundary
+than any FP32 sum can move it (checked on the CPU), the kernel rounds every
+intermediate as the oracle does, and each element of its result is held to
+the last pass's own FP32 sum bound (~1e-6 of the solution, 1000x below the
+TF32 error).  With FP64 refinement sweeps the tier converges like any other:
 5 sweeps reach the FP64 oracle to 1e-12.
 
 Table 10 (Section 3.7) on the GPU: the tier's TF32 l2 errors against the
@@ -87,6 +92,78 @@ def test_tf32_bare_matches_the_rounded_oracle(sem3d, i):
     e_gpu, e_emul = _rel(got, exact), _rel(emul, exact)
     assert 0.6 * e_emul <= e_gpu <= 1.6 * e_emul, (e_gpu, e_emul)
     assert e_gpu < 3e-3
+
+
+# Element-wise parity of the bare tier on grids where no rounding can flip.
+# The kernel's FP32 sums differ from the oracle's FP64 sums by at most
+# 4 K 2^-24 sum|terms| per output (K products per sum; a generous bound for any
+# summation order or accumulator rounding), the division pass also by its FP32
+# lambda sums and fast divide (2^-19 relative).  If every intermediate that is
+# rounded to TF32 lies farther than that from a TF32 rounding boundary (a
+# midpoint between neighbouring TF32 numbers), the kernel rounds every
+# intermediate to the same TF32 number as the oracle, and its result differs
+# from the oracle's, element by element, only by the last pass's own FP32 sums.
+# The cases are the (grid, seed) pairs for which the margins hold (found on the
+# CPU; the test checks the precondition before comparing).
+U32 = 2.0 ** -24
+
+
+def _tf32_margin(x):
+    """Distance from x to the nearest TF32 rounding boundary."""
+    x = np.abs(np.asarray(x, dtype=np.float64))
+    _, e = np.frexp(x)
+    e = np.maximum(e, -125)
+    q = np.ldexp(x, 11 - e)
+    return np.abs(q - np.floor(q) - 0.5) * np.ldexp(1.0, e - 11)
+
+
+def _flip_free_bound(F, axes, c):
+    """The rounded oracle solve and the per-element bound on |kernel - oracle|
+    when no intermediate can round differently (None otherwise)."""
+    from oracle import tf32_operand
+    from oracle.sem import mode_product
+
+    recs = []
+
+    def rnd(a):
+        recs.append(np.asarray(a, dtype=np.float64).copy())
+        return tf32_operand(a)
+
+    emul = fast_solve_rounded(F, *axes, c, rnd=rnd)
+    # rounding points in order: F^T; then per pass the matrix and (passes 1-5) the output
+    d = axes[0].lam[:, None, None] + axes[1].lam[None, :, None] + axes[2].lam[None, None, :] + c
+    U, i = tf32_operand(recs[0]), 1
+    for p in range(6):
+        W = tf32_operand(recs[i])
+        i += 1
+        absum = mode_product(np.abs(U), np.abs(W), p % 3)
+        bound = 4 * W.shape[1] * U32 * absum
+        if p == 5:
+            return emul, np.ascontiguousarray(bound.T)
+        x = recs[i]
+        i += 1
+        slack = bound / np.abs(d) + np.abs(x) * 2.0 ** -19 if p == 2 else bound + np.abs(x) * 2.0 ** -23
+        if np.any(_tf32_margin(x) <= slack):
+            return emul, None
+        U = tf32_operand(x)
+
+
+@pytest.mark.parametrize("n3,k,seed", [((1, 3, 7), 2, 2), ((1, 3, 7), 2, 13), ((3, 3, 3), 1, 0), ((3, 3, 3), 1, 6),
+                                       ((5, 3, 3), 1, 4), ((5, 3, 3), 1, 6)])
+def test_tf32_bare_elementwise_where_no_rounding_can_flip(sem3d, n3, k, seed):
+    axes = [sem_1d(k, (n + 1) // k, 0.0, 1.0) for n in n3]
+    F = random_rhs(*n3, seed=seed)
+    emul, bound = _flip_free_bound(F, axes, 1.0)
+    assert bound is not None, "an intermediate lies within the FP32 sum error of a TF32 rounding boundary"
+    with sem3d.Plan(*n3, k, (1.0, 1.0, 1.0), 1.0) as p:
+        p.set_precision("tf32", 0)
+        f = torch.from_numpy(F).cuda()
+        u = torch.empty_like(f)
+        p.solve(f, u)
+        p.sync_check()
+        got = u.cpu().numpy()
+    excess = np.abs(got - emul) - bound
+    assert np.all(excess <= 0), (float(excess.max()), float(np.abs(got - emul).max()))
 
 
 @pytest.mark.parametrize("i", [2, 3, 5, 7])
