@@ -167,7 +167,7 @@ sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode);
  *                       rounding of that sum (normwise: nodes where |u| is
  *                       far below max |u| get the field's absolute
  *                       resolution).
- *                       Dirichlet plans with k in {1, 2, 4}; other plans use
+ *                       Dirichlet plans with k <= 8; other plans use
  *                       FP64 arithmetic.  Inf or NaN in u or f gives a NaN
  *                       residual.
  *   SEM3D_EXACT_FP64  : FP64 fused multiply-adds.

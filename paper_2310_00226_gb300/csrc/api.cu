@@ -70,7 +70,7 @@ struct sem3d_plan {
   int sweeps = 1;
   int residual = SEM3D_RESIDUAL_MIXED;  // arithmetic of the refinement residuals (BF16X3 tier)
   // FP64-accurate residuals of the split tiers: 64-bit fixed point on the
-  // integer pipe (fix_ok: Dirichlet, k in {1, 2, 4}) unless exact_kind says FP64
+  // integer pipe (fix_ok: Dirichlet, k <= 8) unless exact_kind says FP64
   FixCoef fix{};
   bool fix_ok = false;
   int exact_kind = SEM3D_EXACT_FIXED;

@@ -273,6 +273,124 @@ __global__ void __launch_bounds__(256, 4) stencil_fix4_kernel(FixArgs a, const _
   }
 }
 
+// Fixed-point residual for the other k <= 8 (Dirichlet rows), in the element
+// layout of the FP64 residual: a thread owns the K nodes g = ex*K + q of
+// element ex of one (j, l) line (unknowns i0 + q, i0 = ex*K - 1; q = 0 is the
+// vertex shared with element ex-1), keeps the 2K+1 x-neighbours in registers
+// with every node's x row known at compile time, and reads the y and z rows
+// from the term tables at its (j, l).  The thread of a line's last element
+// also writes the line's pad columns (zeros).  Same arithmetic as
+// stencil_fix4_kernel.
+template <int K>
+__global__ void __launch_bounds__(256) stencil_fix_elem_kernel(FixArgs a, const __grid_constant__ FixCoef cf,
+                                                               int nex) {
+  constexpr int BW = 2 * K + 1;
+  const long long lines = (long long)a.ny * a.nz;
+  const long long total = (long long)nex * lines;
+  const int s = fixed_scale(a.state, cf.t);
+  const int sF = s + cf.t - 56;
+  const int X = -sF;
+  const bool finite = a.state[0] < 2047 && a.state[1] < 2047;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(t % nex);
+    const long long jl = t / nex;
+    const int j = (int)(jl % a.ny), l = (int)(jl / a.ny);
+    const long long row = jl * a.Px;  // this line in Uh, Ul and the output (pitch Px)
+    const int i0 = ex * K - 1;
+    int wh[BW], wl[BW], ws[BW];
+#pragma unroll
+    for (int d = 0; d < BW; ++d) {
+      const int i = i0 - K + d;
+      const bool ok = i >= 0 && i < a.nx;
+      wh[d] = ok ? __ldg(a.Uh + row + i) : 0;
+      wl[d] = ok ? __ldg(a.Ul + row + i) : 0;
+      ws[d] = corr_u(wh[d]);
+    }
+    long long P2[K], P1[K];
+    int Q[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) { P2[q] = 0; P1[q] = 0; Q[q] = 0; }
+    // x: the rows of the element's nodes, known at compile time
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+#pragma unroll
+      for (int e = 0; e < K + 1; ++e) {
+        if (e >= fix_terms(K, q)) break;
+        const int dA = fix_da(K, q, e), dB = fix_db(K, q, e);
+        const int ch = cf.ch[0][q * BW + e], cl = cf.cl[0][q * BW + e];
+        Q[q] += cf.e[0][q * BW + e] * ws[K + q + dA];
+        if (dB == kNoRow) {
+          fx1(P2[q], P1[q], ch, cl, wh[K + q + dA], wl[K + q + dA]);
+        } else {
+          fx1(P2[q], P1[q], ch, cl, wh[K + q + dA] + wh[K + q + dB], wl[K + q + dA] + wl[K + q + dB]);
+          P1[q] += (long long)cf.dc[0][q * BW + e] * wh[K + q + dB];
+          Q[q] += cf.eb[0][q * BW + e] * ws[K + q + dB];
+        }
+      }
+    }
+    // y and z: the rows of the neighbouring lines
+#pragma unroll
+    for (int ax = 1; ax < 3; ++ax) {
+      const int pos = ax == 1 ? j : l;
+      const int lim = ax == 1 ? a.ny : a.nz;
+      const long long stride = ax == 1 ? (long long)a.Px : (long long)a.ny * a.Px;
+      const int qa = (pos + 1) % K;
+      const int nt = fix_terms(K, qa);
+      for (int e = 0; e < nt; ++e) {
+        const int dA = fix_da(K, qa, e), dB = fix_db(K, qa, e);
+        const int ch = cf.ch[ax][qa * BW + e], cl = cf.cl[ax][qa * BW + e], ea = cf.e[ax][qa * BW + e];
+        const bool okA = pos + dA >= 0 && pos + dA < lim;
+        const bool okB = dB != kNoRow && pos + dB >= 0 && pos + dB < lim;
+        const int dc = dB != kNoRow ? cf.dc[ax][qa * BW + e] : 0, eb = dB != kNoRow ? cf.eb[ax][qa * BW + e] : 0;
+        const long long ra = row + dA * stride, rb = row + (dB != kNoRow ? dB : 0) * stride;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int i = i0 + q;
+          if (i < 0) continue;
+          int uh = okA ? __ldg(a.Uh + ra + i) : 0, ul = okA ? __ldg(a.Ul + ra + i) : 0;
+          Q[q] += ea * corr_u(uh);
+          if (dB != kNoRow) {
+            const int bh = okB ? __ldg(a.Uh + rb + i) : 0, bl = okB ? __ldg(a.Ul + rb + i) : 0;
+            P1[q] += (long long)dc * bh;
+            Q[q] += eb * corr_u(bh);
+            uh += bh;
+            ul += bl;
+          }
+          fx1(P2[q], P1[q], ch, cl, uh, ul);
+        }
+      }
+    }
+    const double* frow = a.f + jl * a.nx;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int i = i0 + q;
+      if (i < 0) continue;
+      const long long T = P2[q] + ((P1[q] + ((long long)Q[q] << 3) + kHalf) >> kChunk);
+      const long long F = f64_to_fixed(__ldg(frow + i), sF);
+      const float r = finite ? fixed_to_f32(F - T, X) : __int_as_float(0x7FC00000);
+      const __nv_bfloat16 h16 = __float2bfloat16_rn(r);
+      a.hi[row + i] = h16;
+      a.lo[row + i] = __float2bfloat16_rn(r - __bfloat162float(h16));
+    }
+    if (ex == nex - 1)
+      for (int i = a.nx; i < a.Px; ++i) {
+        a.hi[row + i] = __float2bfloat16_rn(0.f);
+        a.lo[row + i] = __float2bfloat16_rn(0.f);
+      }
+  }
+}
+
+template <int K>
+cudaError_t launch_fix_elem(const FixArgs& a, const FixCoef& cf, cudaStream_t s) {
+  const int nex = (a.nx + 1) / K;
+  const long long total = (long long)nex * a.ny * a.nz;
+  long long b = (total + 255) / 256;  // one thread per element and line, in order (see launch_fix4)
+  if (b > 0x7FFFFFFFLL) b = 0x7FFFFFFFLL;
+  stencil_fix_elem_kernel<K><<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(a, cf, nex);
+  return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_fix4(const FixArgs& a, const FixCoef& cf, cudaStream_t s) {
   // one block per 8 consecutive lines, no grid stride (the resident blocks
@@ -287,7 +405,7 @@ cudaError_t launch_fix4(const FixArgs& a, const FixCoef& cf, cudaStream_t s) {
 }  // namespace
 
 bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf) {
-  if (k != 1 && k != 2 && k != 4) return false;
+  if (k < 1 || k > 8) return false;
   const int bw = 2 * k + 1;
   // one scale for all axes: the largest sum of |H| over the terms of a node
   double rsum = 0.0;
@@ -341,7 +459,7 @@ bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf) {
 cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const double* u, const double* f,
                                   int* state, bool f_exponent_known, int* Uh, int* Ul, __nv_bfloat16* out_hi,
                                   __nv_bfloat16* out_lo, int num_sms, cudaStream_t s) {
-  if (g.bc != 0 || (k != 1 && k != 2 && k != 4)) return cudaErrorInvalidValue;
+  if (g.bc != 0 || k < 1 || k > 8) return cudaErrorInvalidValue;
   const long long N = (long long)g.nx * g.ny * g.nz;
   const long long lines = (long long)g.ny * g.nz;
   const int red_grid = num_sms * 8;
@@ -358,9 +476,14 @@ cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const
   a.Uh = Uh; a.Ul = Ul; a.f = f; a.hi = out_hi; a.lo = out_lo; a.state = state;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
   switch (k) {
-    case 1: return launch_fix4<1>(a, cf, s);
+    case 1: return launch_fix4<1>(a, cf, s);  // 4 % k == 0: the vector layout
     case 2: return launch_fix4<2>(a, cf, s);
-    default: return launch_fix4<4>(a, cf, s);
+    case 4: return launch_fix4<4>(a, cf, s);
+    case 3: return launch_fix_elem<3>(a, cf, s);
+    case 5: return launch_fix_elem<5>(a, cf, s);
+    case 6: return launch_fix_elem<6>(a, cf, s);
+    case 7: return launch_fix_elem<7>(a, cf, s);
+    default: return launch_fix_elem<8>(a, cf, s);
   }
 }
 

@@ -232,12 +232,12 @@ __host__ __device__ constexpr int fix_db(int K, int q, int e) { return (fix_fold
 // in balanced 28-bit chunks C = ch 2^28 + cl, entry [q * (2k+1) + e] for term
 // e; e = round((H 2^t - C) 2^14), the rounded fraction; for a mirrored pair
 // dc = C_{-d} - C_{+d} and eb the fraction of C_{-d}.  A kernel parameter.
-struct FixCoef {
-  int ch[3][4 * 9];
-  int cl[3][4 * 9];
-  int dc[3][4 * 9];
-  int e[3][4 * 9];
-  int eb[3][4 * 9];
+struct FixCoef {  // 8 KB: a kernel parameter (CUDA 12.1+ allows 32 KB)
+  int ch[3][8 * 17];
+  int cl[3][8 * 17];
+  int dc[3][8 * 17];
+  int e[3][8 * 17];
+  int eb[3][8 * 17];
   int t;
 };
 struct FixArgs {
@@ -250,13 +250,13 @@ struct FixArgs {
   int nx, ny, nz, Px;
 };
 // Build the tables from the FP64 rows hq[axis] (k x (2k+1), x with c on its
-// diagonal).  False for k not in {1, 2, 4} or rows that are not mirror-
-// symmetric up to rounding (the fixed-point residual is then not used).
+// diagonal).  False for k > 8 or rows that are not mirror-symmetric up to
+// rounding (the fixed-point residual is then not used).
 bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf);
 // r = f - (c + H_x (+) H_y (+) H_z) u evaluated exactly in 64-bit integer
 // fixed point (error below FP64 rounding of the terms), written as bf16 hi/lo
 // at pitch Px with zero pads, like launch_stencil mode 2.  Dirichlet rows and
-// k in {1, 2, 4} only (cudaErrorInvalidValue otherwise).  state: 2 device ints
+// 1 <= k <= 8 only (cudaErrorInvalidValue otherwise).  state: 2 device ints
 // (the max exponents of u and f; f's is taken as given when f_exponent_known,
 // e.g. from launch_split's emax); Uh,
 // Ul: two int32 arrays of Px * ny * nz (the fixed-point u, 16-byte aligned).

@@ -4,14 +4,15 @@ r = f - (c + H_x (+) H_y (+) H_z) u (Eq. 12) evaluated with exact integer
 products and sums on one power-of-two scale per field; its error is below one
 FP64 rounding of the largest sum of |H||u| (normwise).  Checked here through
 the refined solves that use it:
-  * against the FP64 oracle at 1e-12 (relative L-inf), k in {1, 2, 4}, grids
+  * against the FP64 oracle at 1e-12 (relative L-inf), k in {1, 2, 4} (vector
+    layout) and 3, 5, 6, 7, 8 (element layout), grids
     with partial 4-node chunks and short axes, both schedules that use it
     (the last sweep of "mixed", every sweep of "fp64"), BF16X3 and BF16;
   * against the same solve with FP64-FMA residuals (the two arithmetics agree
     to the refinement's floor);
   * power-of-two scaling of f scales u exactly (the scales are found on the
     device from the fields' exponents, so every integer is the same);
-  * NaN in f reaches u; plans it does not serve (k = 3, Neumann data, the
+  * NaN in f reaches u; plans it does not serve (k > 8, Neumann data, the
     TF32 tier) report FP64.
 """
 
@@ -68,6 +69,27 @@ def test_fixed_point_residual_matches_oracle(sem3d, case, prec, sweeps, residual
     assert kind == "fixed"
     assert np.isfinite(got).all()
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12, float(np.abs(got - ref).max() / np.abs(ref).max())
+
+
+# k not dividing 4: the element-layout kernel (one thread per element and line)
+ELEM_CASES = [((29, 17, 23), 3, (1.0, 0.8, 1.2), 1.0), ((39, 29, 19), 5, (1.0, 1.0, 1.0), 0.5),
+              ((47, 35, 23), 6, (1.0, 1.0, 1.0), 2.0), ((27, 41, 13), 7, (1.0, 1.5, 0.5), 1.0),
+              ((63, 31, 47), 8, (1.0, 1.0, 1.0), 0.0)]
+
+
+@pytest.mark.parametrize("case", range(len(ELEM_CASES)))
+@pytest.mark.parametrize("sweeps,residual", [(3, "mixed"), (2, "fp64")])
+def test_fixed_point_residual_element_layout(sem3d, case, sweeps, residual):
+    n3, k, L3, c = ELEM_CASES[case]
+    F = random_rhs(*n3, seed=340 + case)
+    axes = [sem_1d(k, (n + 1) // k, 0.0, Lb) for n, Lb in zip(n3, L3)]
+    ref = refined_solve(F, *axes, c, 1)
+    got, kind = _solve(sem3d, n3, k, L3, c, F, "bf16x3", sweeps, residual, "fixed")
+    assert kind == "fixed"
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12, float(np.abs(got - ref).max() / np.abs(ref).max())
+    fp, _ = _solve(sem3d, n3, k, L3, c, F, "bf16x3", sweeps, residual, "fp64")
+    assert np.abs(got - fp).max() / np.abs(fp).max() < 1e-13
 
 
 @pytest.mark.parametrize("case", [0, 1, 2])
@@ -137,7 +159,10 @@ def test_kind_reporting(sem3d):
         assert p.exact_residual_kind() == "fp64"  # TF32 tier: FP64 residuals
     with sem3d.Plan(29, 29, 29, 3, (1.0, 1.0, 1.0), 1.0) as p:
         p.set_precision("bf16x3", 3)
-        assert p.exact_residual_kind() == "fp64"  # k = 3
+        assert p.exact_residual_kind() == "fixed"  # k = 3: the element-layout kernel
+    with sem3d.Plan(35, 35, 35, 9, (1.0, 1.0, 1.0), 1.0) as p:
+        p.set_precision("bf16x3", 3)
+        assert p.exact_residual_kind() == "fp64"  # k > 8
     with sem3d.Plan(33, 33, 33, 4, (1.0, 1.0, 1.0), 1.0, bc="neumann") as p:
         p.set_precision("bf16x3", 3)
         assert p.exact_residual_kind() == "fp64"  # Neumann rows
