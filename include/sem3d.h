@@ -151,10 +151,10 @@ sem3d_status sem3d_set_precision(sem3d_handle h, sem3d_precision p, int sweeps);
 typedef enum { SEM3D_RESIDUAL_FP64 = 0, SEM3D_RESIDUAL_MIXED = 1, SEM3D_RESIDUAL_DF = 2 } sem3d_residual;
 sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode);
 
-/* How the split tiers (SEM3D_BF16X3, SEM3D_BF16) evaluate their FP64-accurate
- * residuals (every sweep of SEM3D_RESIDUAL_FP64, the last sweep of
- * SEM3D_RESIDUAL_MIXED) -- the same r = f - (c + H_x (+) H_y (+) H_z) u of
- * Eq. 12 either way:
+/* How the split tiers (SEM3D_BF16X3, SEM3D_BF16) and the TF32 tier evaluate
+ * their FP64-accurate residuals (split tiers: every sweep of
+ * SEM3D_RESIDUAL_FP64, the last sweep of SEM3D_RESIDUAL_MIXED; TF32: every
+ * sweep) -- the same r = f - (c + H_x (+) H_y (+) H_z) u of Eq. 12 either way:
  *   SEM3D_EXACT_FIXED : (default) exactly in 64-bit integer fixed point on
  *                       the integer pipe: u and f scaled by one power of two
  *                       per field (found on the device from their largest
@@ -172,7 +172,7 @@ sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode);
  *                       residual.
  *   SEM3D_EXACT_FP64  : FP64 fused multiply-adds.
  * sem3d_exact_residual_kind reports the arithmetic the plan's current tier
- * and geometry use (SEM3D_EXACT_FP64 for tiers other than the split ones).
+ * and geometry use (SEM3D_EXACT_FP64 for the FP64, FP32 and F16X3 tiers).
  * Errors: SEM3D_ERR_INVALID_ARG for a NULL handle / pointer or unknown kind. */
 typedef enum { SEM3D_EXACT_FIXED = 0, SEM3D_EXACT_FP64 = 1 } sem3d_exact_residual;
 sem3d_status sem3d_set_exact_residual(sem3d_handle h, sem3d_exact_residual kind);

@@ -558,6 +558,14 @@ sem3d_status sem3d_set_residual(sem3d_handle h, sem3d_residual mode) {
   return SEM3D_OK;
 }
 
+}  // extern "C"
+
+namespace {
+bool use_fixed_residual(const sem3d_plan* h);  // FP64-accurate residuals in fixed point (defined below)
+}  // namespace
+
+extern "C" {
+
 sem3d_status sem3d_set_exact_residual(sem3d_handle h, sem3d_exact_residual kind) {
   if (!h) return fail(SEM3D_ERR_INVALID_ARG, "handle is NULL");
   if (kind != SEM3D_EXACT_FIXED && kind != SEM3D_EXACT_FP64) return fail(SEM3D_ERR_INVALID_ARG, "unknown kind");
@@ -567,8 +575,7 @@ sem3d_status sem3d_set_exact_residual(sem3d_handle h, sem3d_exact_residual kind)
 
 sem3d_status sem3d_exact_residual_kind(sem3d_handle h, int* kind) {
   if (!h || !kind) return fail(SEM3D_ERR_INVALID_ARG, "NULL argument");
-  const bool split = h->prec == SEM3D_BF16X3 || h->prec == SEM3D_BF16;
-  *kind = (split && h->fix_ok && h->exact_kind == SEM3D_EXACT_FIXED) ? SEM3D_EXACT_FIXED : SEM3D_EXACT_FP64;
+  *kind = use_fixed_residual(h) ? SEM3D_EXACT_FIXED : SEM3D_EXACT_FP64;
   return SEM3D_OK;
 }
 
@@ -650,7 +657,8 @@ namespace {
 // The solve itself (arguments already checked, workspace present).
 // FP64-accurate residuals of the split tiers in 64-bit fixed point (see fix_kernels.cu)
 bool use_fixed_residual(const sem3d_plan* h) {
-  return h->fix_ok && h->exact_kind == SEM3D_EXACT_FIXED && (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_BF16);
+  return h->fix_ok && h->exact_kind == SEM3D_EXACT_FIXED &&
+         (h->prec == SEM3D_BF16X3 || h->prec == SEM3D_BF16 || h->prec == SEM3D_TF32);
 }
 
 sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s) {
@@ -673,8 +681,18 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
   } else if (h->prec == SEM3D_TF32) {
     double* r = reinterpret_cast<double*>(static_cast<char*>(h->ws) + 2 * align256(tf32_elems(h->g) * sizeof(float)));
     if ((st = solve_once_tf32(h, f, u, false, s)) != SEM3D_OK) return st;
+    // between solves the two ping-pong buffers (>= Px ny nz floats each) are
+    // free: they hold u in fixed point for the fixed-point residual
+    int* Uh = static_cast<int*>(h->ws);
+    int* Ul = reinterpret_cast<int*>(static_cast<char*>(h->ws) + align256(tf32_elems(h->g) * sizeof(float)));
+    const bool fixed = use_fixed_residual(h);
     for (int sw = 0; sw < h->sweeps; ++sw) {
-      LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
+      if (fixed)
+        LAUNCH(h, K_STENCIL, sw == 0 ? 4 : 3, s,
+               launch_residual_fixed(h->g, h->k, h->fix, u, f, h->d_fix, sw > 0, Uh, Ul, nullptr, nullptr,
+                                     h->num_sms, s, r));
+      else
+        LAUNCH(h, K_STENCIL, 1, s, launch_stencil(h->g, h->k, h->dev, u, f, r, nullptr, nullptr, 1, s));
       if ((st = solve_once_tf32(h, r, u, true, s)) != SEM3D_OK) return st;
     }
   } else {

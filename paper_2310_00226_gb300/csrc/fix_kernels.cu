@@ -248,15 +248,24 @@ __global__ void __launch_bounds__(256, 4) stencil_fix4_kernel(FixArgs a, const _
           fx_term(P2, P1, ch, cl, vh, vl);
         }
       }
-      float r[4];
+      long long R[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        if (i0 + p >= a.nx) { r[p] = 0.f; continue; }  // pads stay zero
         // sum (C + E 2^-14) U / 2^56, rounded once (Q E-units are 2^31 = 8 x 2^28)
         const long long T = P2[p] + ((P1[p] + ((long long)Q[p] << 3) + kHalf) >> kChunk);
-        const long long F = f64_to_fixed(__ldg(frow + i0 + p), sF);
-        r[p] = finite ? fixed_to_f32(F - T, X) : __int_as_float(0x7FC00000);
+        R[p] = (i0 + p < a.nx) ? f64_to_fixed(__ldg(frow + i0 + p), sF) - T : 0;
       }
+      if (a.out64) {  // FP64 r at pitch nx
+        double* orow = a.out64 + line * a.nx;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+          if (i0 + p < a.nx) orow[i0 + p] = finite ? ldexp((double)R[p], X) : __longlong_as_double(0x7FF8000000000000LL);
+        continue;
+      }
+      float r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)  // pads stay zero
+        r[p] = (i0 + p >= a.nx) ? 0.f : finite ? fixed_to_f32(R[p], X) : __int_as_float(0x7FC00000);
       const long long o = line * a.Px + i0;
       uint32_t hw[2], lw[2];
 #pragma unroll
@@ -367,13 +376,17 @@ __global__ void __launch_bounds__(256) stencil_fix_elem_kernel(FixArgs a, const 
       const int i = i0 + q;
       if (i < 0) continue;
       const long long T = P2[q] + ((P1[q] + ((long long)Q[q] << 3) + kHalf) >> kChunk);
-      const long long F = f64_to_fixed(__ldg(frow + i), sF);
-      const float r = finite ? fixed_to_f32(F - T, X) : __int_as_float(0x7FC00000);
+      const long long R = f64_to_fixed(__ldg(frow + i), sF) - T;
+      if (a.out64) {  // FP64 r at pitch nx
+        a.out64[jl * a.nx + i] = finite ? ldexp((double)R, X) : __longlong_as_double(0x7FF8000000000000LL);
+        continue;
+      }
+      const float r = finite ? fixed_to_f32(R, X) : __int_as_float(0x7FC00000);
       const __nv_bfloat16 h16 = __float2bfloat16_rn(r);
       a.hi[row + i] = h16;
       a.lo[row + i] = __float2bfloat16_rn(r - __bfloat162float(h16));
     }
-    if (ex == nex - 1)
+    if (ex == nex - 1 && !a.out64)
       for (int i = a.nx; i < a.Px; ++i) {
         a.hi[row + i] = __float2bfloat16_rn(0.f);
         a.lo[row + i] = __float2bfloat16_rn(0.f);
@@ -458,7 +471,7 @@ bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf) {
 
 cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const double* u, const double* f,
                                   int* state, bool f_exponent_known, int* Uh, int* Ul, __nv_bfloat16* out_hi,
-                                  __nv_bfloat16* out_lo, int num_sms, cudaStream_t s) {
+                                  __nv_bfloat16* out_lo, int num_sms, cudaStream_t s, double* out64) {
   if (g.bc != 0 || k < 1 || k > 8) return cudaErrorInvalidValue;
   const long long N = (long long)g.nx * g.ny * g.nz;
   const long long lines = (long long)g.ny * g.nz;
@@ -473,7 +486,7 @@ cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const
   to_fixed_kernel<<<(unsigned)(cb < 1 ? 1 : cb), 256, 0, s>>>(u, Uh, Ul, g.nx, g.Px, lines, state, cf.t);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   FixArgs a{};
-  a.Uh = Uh; a.Ul = Ul; a.f = f; a.hi = out_hi; a.lo = out_lo; a.state = state;
+  a.Uh = Uh; a.Ul = Ul; a.f = f; a.hi = out_hi; a.lo = out_lo; a.state = state; a.out64 = out64;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.Px = g.Px;
   switch (k) {
     case 1: return launch_fix4<1>(a, cf, s);  // 4 % k == 0: the vector layout

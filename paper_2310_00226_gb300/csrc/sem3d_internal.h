@@ -247,6 +247,7 @@ struct FixArgs {
   __nv_bfloat16* hi;
   __nv_bfloat16* lo;
   const int* state;  // [0]: max biased exponent of u, [1]: of f
+  double* out64;     // if set: r in FP64 at pitch nx (hi / lo unused)
   int nx, ny, nz, Px;
 };
 // Build the tables from the FP64 rows hq[axis] (k x (2k+1), x with c on its
@@ -260,9 +261,11 @@ bool build_fix_coef(const double* const hq[3], int k, FixCoef& cf);
 // (the max exponents of u and f; f's is taken as given when f_exponent_known,
 // e.g. from launch_split's emax); Uh,
 // Ul: two int32 arrays of Px * ny * nz (the fixed-point u, 16-byte aligned).
+// With out64 set, r is written in FP64 at pitch nx instead (the TF32 tier's
+// refinement reads it so).
 cudaError_t launch_residual_fixed(const Geom& g, int k, const FixCoef& cf, const double* u, const double* f,
                                   int* state, bool f_exponent_known, int* Uh, int* Ul, __nv_bfloat16* out_hi,
-                                  __nv_bfloat16* out_lo, int num_sms, cudaStream_t s);
+                                  __nv_bfloat16* out_lo, int num_sms, cudaStream_t s, double* out64 = nullptr);
 // FP64 dense n-pitch -> bf16 hi/lo at pitch Px with zero pads; with emax
 // set, also atomicMax(*emax, largest biased FP64 exponent of the input).
 cudaError_t launch_split(const Geom& g, const double* in, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,

@@ -12,8 +12,9 @@ the refined solves that use it:
     to the refinement's floor);
   * power-of-two scaling of f scales u exactly (the scales are found on the
     device from the fields' exponents, so every integer is the same);
+  * the TF32 tier's sweeps (FP64 output), against the oracle and FP64 FMAs;
   * NaN in f reaches u; plans it does not serve (k > 8, Neumann data, the
-    TF32 tier) report FP64.
+    FP32 tier) report FP64.
 """
 
 import numpy as np
@@ -92,6 +93,21 @@ def test_fixed_point_residual_element_layout(sem3d, case, sweeps, residual):
     assert np.abs(got - fp).max() / np.abs(fp).max() < 1e-13
 
 
+@pytest.mark.parametrize("n3,k", [((63, 47, 95), 4), ((29, 17, 23), 3)])
+def test_tf32_tier_with_fixed_point_residuals(sem3d, n3, k):
+    # the TF32 tier's sweeps read r in FP64 (the kernels' FP64 output mode)
+    L3, c = (1.0, 0.9, 1.1), 1.5
+    F = random_rhs(*n3, seed=350 + k)
+    axes = [sem_1d(k, (n + 1) // k, 0.0, Lb) for n, Lb in zip(n3, L3)]
+    ref = refined_solve(F, *axes, c, 1)
+    got, kind = _solve(sem3d, n3, k, L3, c, F, "tf32", 6, "mixed", "fixed")
+    assert kind == "fixed"
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12, float(np.abs(got - ref).max() / np.abs(ref).max())
+    fp, kind = _solve(sem3d, n3, k, L3, c, F, "tf32", 6, "mixed", "fp64")
+    assert kind == "fp64"
+    assert np.abs(got - fp).max() / np.abs(fp).max() < 1e-13
+
+
 @pytest.mark.parametrize("case", [0, 1, 2])
 def test_fixed_point_and_fp64_residuals_agree(sem3d, case):
     n3, k, L3, c = CASES[case]
@@ -156,7 +172,9 @@ def test_kind_reporting(sem3d):
         assert p.exact_residual_kind() == "fp64"
         p.set_precision("tf32", 3)
         p.set_exact_residual("fixed")
-        assert p.exact_residual_kind() == "fp64"  # TF32 tier: FP64 residuals
+        assert p.exact_residual_kind() == "fixed"  # TF32 tier: every sweep
+        p.set_precision("fp32", 2)
+        assert p.exact_residual_kind() == "fp64"  # FP32 tier: FP64 residuals
     with sem3d.Plan(29, 29, 29, 3, (1.0, 1.0, 1.0), 1.0) as p:
         p.set_precision("bf16x3", 3)
         assert p.exact_residual_kind() == "fixed"  # k = 3: the element-layout kernel
