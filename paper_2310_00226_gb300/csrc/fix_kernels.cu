@@ -8,7 +8,7 @@
 // saturated.
 //
 // Representation.  With one power-of-two scale for the whole field, u is held
-// as U = round(u 2^s) with |U| < 2^57 and every row of H (all three axes and
+// as U = round(u 2^s) with |U| <= 2^57 and every row of H (all three axes and
 // c, sharing one scale) as C + E 2^-14 with integers C = round(H 2^t),
 // whose magnitudes over the terms of any node sum to about 2^58, and E the
 // rounded fraction H 2^t - C.  U and C are split into balanced chunks
@@ -20,7 +20,8 @@
 // the last part, below 2^54 per term and of mean zero, is dropped.  The
 // correction joins the 2^28 sum before its one rounding, f is rounded to the
 // same fixed point, the difference F - T is exact, and the residual is
-// converted to FP32 (the next solve reads it as split bf16).
+// converted to FP32 and split to bf16 (the split tiers' next solve reads it
+// so) or to FP64 (the TF32 tier's).
 //
 // Every rounding is to nearest: the operator's conditioning amplifies the
 // smooth (low-frequency) part of a residual error by up to 1/lambda_min, so a
