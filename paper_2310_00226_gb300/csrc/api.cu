@@ -745,14 +745,14 @@ sem3d_status run_solve(sem3d_plan* h, const double* f, double* u, cudaStream_t s
         if (f16) {
           if ((st = reset_scales()) != SEM3D_OK) return st;
           LAUNCH(h, K_STENCIL, 1, s,
-                 launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16, exact_coef));
+                 launch_stencil_df(h->g, h->k, h->dev, D, f, nullptr, nullptr, s, r32, h->d_f16, exact_coef, q == 1));
           LAUNCH(h, K_SPLIT, 1, s, launch_split_f16(h->g, r32, false, S0h, S0l, h->d_f16, s));
         } else {
           // k in {1, 2, 4}: one vector kernel that also writes the pads; otherwise
           // the element kernel plus a pad-zeroing kernel when Px > nx
           const int df_launches = (h->k == 1 || h->k == 2 || h->k == 4 || h->g.Px == h->g.nx) ? 1 : 2;
           LAUNCH(h, K_STENCIL, df_launches, s,
-                 launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s, nullptr, nullptr, exact_coef));
+                 launch_stencil_df(h->g, h->k, h->dev, D, f, S0.hi, S0.lo, s, nullptr, nullptr, exact_coef, q == 1));
         }
         const bool last_df = (q == ndf);
         if ((st = solve_once_bf16x3(h, S0, S1, last_df ? u : nullptr, last_df ? EPI_DF_ACCUM_F64 : EPI_DF_ACCUM, D,
@@ -1413,7 +1413,7 @@ sem3d_status batched_tc(int count, const sem3d_handle* hs, const double* const* 
         const int launches = (h->k == 1 || h->k == 2 || h->k == 4 || h->g.Px == h->g.nx) ? 1 : 2;
         LAUNCH(h, K_STENCIL, launches, fan.stream(q),
                launch_stencil_df(h->g, h->k, h->dev, D[q], f[q], S0[q].hi, S0[q].lo, fan.stream(q), nullptr, nullptr,
-                                 exact_coef));
+                                 exact_coef, sw == 1));
       }
       if ((st = fan.end()) != SEM3D_OK) return st;
       const bool last_df = sw == ndf;

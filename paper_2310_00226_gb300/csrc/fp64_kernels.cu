@@ -357,12 +357,15 @@ __device__ __forceinline__ void f64_to_df(double x, float& hi, float& lo) {
 
 // (ah, al) -= (ch + cl [+ cl2]) * (uh + ul), dropping cl*ul and cl2*ul; the
 // third coefficient term cl2 enters only when EXACT (else the 48-bit ch + cl).
-template <bool EXACT = false>
+// LO0: ul is zero (the solution right after the first solve), and the ch*ul
+// term, exactly 0 there, is not formed (the same result).
+template <bool EXACT = false, bool LO0 = false>
 __device__ __forceinline__ void df_sub_prod(float& ah, float& al, float ch, float cl, float uh, float ul,
                                             float cl2 = 0.f) {
   const float p = ch * uh;
   const float e = fmaf(ch, uh, -p);
-  const float t = fmaf(ch, ul, fmaf(cl, uh, EXACT ? fmaf(cl2, uh, e) : e));
+  const float t0 = fmaf(cl, uh, EXACT ? fmaf(cl2, uh, e) : e);
+  const float t = LO0 ? t0 : fmaf(ch, ul, t0);
   const float s = ah - p;
   const float bb = s - ah;
   const float err = (ah - (s - bb)) - (p + bb);
@@ -499,7 +502,7 @@ struct DfCoef {
 // the line's Px/4 chunks.  Since 4 % k == 0, node 4c+p has the local index
 // (p+1) % k for every c: each position's x row of H is known at compile time
 // and only its band is summed.  The y and z rows depend on the warp's (j, l).
-template <int K, bool EXACT>
+template <int K, bool EXACT, bool LO0>
 __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __grid_constant__ DfCoef cf) {
   constexpr int BW = 2 * K + 1;
   const int lane = threadIdx.x & 31;
@@ -529,10 +532,10 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
       float wh[12], wl[12];
       {
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 ph = c > 0 ? __ldg(UH + row4 + c - 1) : z4, pl = c > 0 ? __ldg(UL + row4 + c - 1) : z4;
-        const float4 ch = __ldg(UH + row4 + c), cl = __ldg(UL + row4 + c);
+        const float4 ph = c > 0 ? __ldg(UH + row4 + c - 1) : z4, pl = (c > 0 && !LO0) ? __ldg(UL + row4 + c - 1) : z4;
+        const float4 ch = __ldg(UH + row4 + c), cl = LO0 ? z4 : __ldg(UL + row4 + c);
         const float4 nh = c + 1 < chunks ? __ldg(UH + row4 + c + 1) : z4;
-        const float4 nl = c + 1 < chunks ? __ldg(UL + row4 + c + 1) : z4;
+        const float4 nl = (c + 1 < chunks && !LO0) ? __ldg(UL + row4 + c + 1) : z4;
         wh[0] = ph.x; wh[1] = ph.y; wh[2] = ph.z; wh[3] = ph.w; wh[4] = ch.x; wh[5] = ch.y;
         wh[6] = ch.z; wh[7] = ch.w; wh[8] = nh.x; wh[9] = nh.y; wh[10] = nh.z; wh[11] = nh.w;
         wl[0] = pl.x; wl[1] = pl.y; wl[2] = pl.z; wl[3] = pl.w; wl[4] = cl.x; wl[5] = cl.y;
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
 #pragma unroll
         for (int d = -K; d <= K; ++d)
           if (d >= dlo && d <= dhi)  // compile-time after unrolling
-            df_sub_prod<EXACT>(ah[p], al[p], cf.h[0][q * BW + d + K], cf.l[0][q * BW + d + K], wh[4 + p + d], wl[4 + p + d],
+            df_sub_prod<EXACT, LO0>(ah[p], al[p], cf.h[0][q * BW + d + K], cf.l[0][q * BW + d + K], wh[4 + p + d], wl[4 + p + d],
                         EXACT ? cf.l2[0][q * BW + d + K] : 0.f);
       }
       // y and z: the rows of the neighbouring lines, one float4 pair per row
@@ -554,11 +557,12 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
         if (d < ylo || d > yhi || j + d < 0 || j + d >= a.ny) continue;  // warp-uniform
         const float chh = cf.h[1][qy * BW + d + K], cll = cf.l[1][qy * BW + d + K];
         const float cl2 = EXACT ? cf.l2[1][qy * BW + d + K] : 0.f;
-        const float4 vh = __ldg(UH + row4 + (long long)d * chunks + c), vl = __ldg(UL + row4 + (long long)d * chunks + c);
-        df_sub_prod<EXACT>(ah[0], al[0], chh, cll, vh.x, vl.x, cl2);
-        df_sub_prod<EXACT>(ah[1], al[1], chh, cll, vh.y, vl.y, cl2);
-        df_sub_prod<EXACT>(ah[2], al[2], chh, cll, vh.z, vl.z, cl2);
-        df_sub_prod<EXACT>(ah[3], al[3], chh, cll, vh.w, vl.w, cl2);
+        const float4 vh = __ldg(UH + row4 + (long long)d * chunks + c);
+        const float4 vl = LO0 ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(UL + row4 + (long long)d * chunks + c);
+        df_sub_prod<EXACT, LO0>(ah[0], al[0], chh, cll, vh.x, vl.x, cl2);
+        df_sub_prod<EXACT, LO0>(ah[1], al[1], chh, cll, vh.y, vl.y, cl2);
+        df_sub_prod<EXACT, LO0>(ah[2], al[2], chh, cll, vh.z, vl.z, cl2);
+        df_sub_prod<EXACT, LO0>(ah[3], al[3], chh, cll, vh.w, vl.w, cl2);
       }
 #pragma unroll
       for (int d = -K; d <= K; ++d) {
@@ -566,11 +570,11 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
         const float chh = cf.h[2][qz * BW + d + K], cll = cf.l[2][qz * BW + d + K];
         const float cl2 = EXACT ? cf.l2[2][qz * BW + d + K] : 0.f;
         const float4 vh = __ldg(UH + row4 + (long long)d * splane + c);
-        const float4 vl = __ldg(UL + row4 + (long long)d * splane + c);
-        df_sub_prod<EXACT>(ah[0], al[0], chh, cll, vh.x, vl.x, cl2);
-        df_sub_prod<EXACT>(ah[1], al[1], chh, cll, vh.y, vl.y, cl2);
-        df_sub_prod<EXACT>(ah[2], al[2], chh, cll, vh.z, vl.z, cl2);
-        df_sub_prod<EXACT>(ah[3], al[3], chh, cll, vh.w, vl.w, cl2);
+        const float4 vl = LO0 ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(UL + row4 + (long long)d * splane + c);
+        df_sub_prod<EXACT, LO0>(ah[0], al[0], chh, cll, vh.x, vl.x, cl2);
+        df_sub_prod<EXACT, LO0>(ah[1], al[1], chh, cll, vh.y, vl.y, cl2);
+        df_sub_prod<EXACT, LO0>(ah[2], al[2], chh, cll, vh.z, vl.z, cl2);
+        df_sub_prod<EXACT, LO0>(ah[3], al[3], chh, cll, vh.w, vl.w, cl2);
       }
       float r[4];
 #pragma unroll
@@ -602,7 +606,7 @@ __global__ void __launch_bounds__(256, 4) stencil_df4_kernel(DfArgs a, const __g
 }
 
 template <int K>
-cudaError_t launch_df4(const DfArgs& a, const DevAxis* ax, bool exact, cudaStream_t s) {
+cudaError_t launch_df4(const DfArgs& a, const DevAxis* ax, bool exact, bool lo_zero, cudaStream_t s) {
   DfCoef cf{};
   for (int w = 0; w < 3; ++w)
     for (int e = 0; e < K * (2 * K + 1); ++e) {
@@ -616,8 +620,14 @@ cudaError_t launch_df4(const DfArgs& a, const DevAxis* ax, bool exact, cudaStrea
   const long long lines = (long long)a.ny * a.nz;
   long long blocks = (lines + 7) / 8;
   if (blocks > 0x7FFFFFFFLL) blocks = 0x7FFFFFFFLL;
-  if (exact) stencil_df4_kernel<K, true><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a, cf);
-  else stencil_df4_kernel<K, false><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a, cf);
+  const unsigned g = (unsigned)(blocks < 1 ? 1 : blocks);
+  if (exact) {
+    if (lo_zero) stencil_df4_kernel<K, true, true><<<g, 256, 0, s>>>(a, cf);
+    else stencil_df4_kernel<K, true, false><<<g, 256, 0, s>>>(a, cf);
+  } else {
+    if (lo_zero) stencil_df4_kernel<K, false, true><<<g, 256, 0, s>>>(a, cf);
+    else stencil_df4_kernel<K, false, false><<<g, 256, 0, s>>>(a, cf);
+  }
   return cudaGetLastError();
 }
 
@@ -756,7 +766,7 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
                               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s, float* out32,
-                              F16State* st, bool exact_coef) {
+                              F16State* st, bool exact_coef, bool lo_zero) {
   if (g.bc != 0) return cudaErrorInvalidValue;  // element-pattern rows (Dirichlet) only
   DfArgs a{};
   a.uh = u.hi; a.ul = u.lo; a.f = f; a.hi = out_hi; a.lo = out_lo;
@@ -769,9 +779,9 @@ cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers
   a.nex = (g.nx + 1) / k;
   cudaError_t e;
   switch (k) {
-    case 1: return launch_df4<1>(a, ax, exact_coef, s);  // pads written as zeros
-    case 2: return launch_df4<2>(a, ax, exact_coef, s);
-    case 4: return launch_df4<4>(a, ax, exact_coef, s);
+    case 1: return launch_df4<1>(a, ax, exact_coef, lo_zero, s);  // pads written as zeros
+    case 2: return launch_df4<2>(a, ax, exact_coef, lo_zero, s);
+    case 4: return launch_df4<4>(a, ax, exact_coef, lo_zero, s);
     case 3: e = launch_df<3>(a, exact_coef, s); break;
     case 5: e = launch_df<5>(a, exact_coef, s); break;
     case 6: e = launch_df<6>(a, exact_coef, s); break;

@@ -209,9 +209,12 @@ cudaError_t launch_stencil(const Geom& g, int k, const DevAxis* ax, const double
 // (48 bits); with exact_coef also the third term lo2, which makes them exact:
 // a 48-bit operator is a different operator, whose solution a refinement with
 // only these residuals would converge to (off by ~kappa * 2^-48).
+// lo_zero: u's low parts are all zero (right after the first solve); the
+// vector kernel (k in {1, 2, 4}) then skips them (the same result).
 cudaError_t launch_stencil_df(const Geom& g, int k, const DevAxis* ax, DfBuffers u, const double* f,
                               __nv_bfloat16* out_hi, __nv_bfloat16* out_lo, cudaStream_t s,
-                              float* out32 = nullptr, F16State* st = nullptr, bool exact_coef = false);
+                              float* out32 = nullptr, F16State* st = nullptr, bool exact_coef = false,
+                              bool lo_zero = false);
 // FP64 residual written as FP32 at pitch Px with its max |r| in state slot 0
 // (the F16X3 tier then splits it with launch_split_f16).  1 <= k <= 8.
 cudaError_t launch_stencil_f32out(const Geom& g, int k, const DevAxis* ax, const double* u, const double* f,
