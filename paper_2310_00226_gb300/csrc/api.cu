@@ -1556,7 +1556,7 @@ struct StaticAddr {
 };
 StaticAddr g_static_addr[kMaxDevices];
 
-// The driver's cuCtxGetCurrent, reached through the runtime's entry-point
+// The CUDA driver API's cuCtxGetCurrent, reached through the runtime's entry-point
 // query (the library links no driver library).
 CUresult current_context(CUcontext* ctx) {
   static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
