@@ -28,10 +28,11 @@
 // rounding that is biased, or one applied to a quantity that changes slowly
 // from node to node (the small correction sum rounded on its own), leaves a
 // coherent error that grows with the grid; the rows' fractions matter for
-// the same reason (an error in a row sum acts like a change of c).  Exact-
-// integer emulation of this arithmetic against exact rational residuals,
-// propagated through the solve: the result's error is that of FP64 residuals
-// at moderate conditioning and ~4x below it with lambda_min + c = 0.03.
+// the same reason (an error in a row sum acts like a change of c).  An exact-
+// integer model of this arithmetic (tests/test_fixed_point_model_cpu.py),
+// against exact rational residuals and propagated through the solve: the
+// result's error is no larger than that of FP64 residuals, also with
+// lambda_min + c a thousandth of lambda_min.
 // The error is absolute (one scale per field): nodes where |u| is far below
 // max |u| get the field's resolution, not FP64's relative one.
 //
